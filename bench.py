@@ -1,0 +1,339 @@
+#!/usr/bin/env python
+"""Benchmark of the differentiable solving stage (fwd+bwd clause-literal evals/s).
+
+One step = one pass of the whole hot path over one batch of candidates: relaxed values,
+forward clause products + loss, backward leave-one-out gradient, Adam update, rounding (all in
+the fused gs_step) and the exact bit-packed check (gs_check_bits). Workload: planted uniform
+random 3-SAT, n = 100,000, m = 426,000, B = 1024 candidates, float32 (the differentiation
+workload). One clause-literal eval = one (literal occurrence, candidate) pair taken through
+forward and backward in a step, so a step is nnz * B evals.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference]
+
+Under torchrun (N > 1) every rank optimises its own batch of candidates of the same formula
+(weak scaling, no data-path collective); timing is the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "differentiation"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=400)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", choices=["native", "reference"], default="native")
+    ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--dtype", default=None, help="override the storage dtype (f32, bf16, f16)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle sample")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------------------------
+def workload_setup(name, dtype_override=None):
+    from paper_2603_28796_b300 import synth
+
+    w = synth.WORKLOADS[name]
+    cnf = synth.workload_cnf(name, seed=0)
+    dtype = dtype_override or w["dtype"]
+    return cnf, int(w["B"]), dtype, w["desc"]
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6400.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while the timed region runs."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = os.path.join("/tmp", "gs_clocks_%d_%d.csv" % (os.getpid(), gpu_index))
+
+    def start(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "50"], stdout=self.f,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        rows = []
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+            try:
+                with open(self.path) as f:
+                    rows = [r.strip().split(", ") for r in f if r.strip()]
+                os.remove(self.path)
+            except Exception:
+                rows = []
+        if not rows:
+            try:
+                out = subprocess.run(["nvidia-smi", "-i", str(self.idx), "--query-gpu=" + self.Q,
+                                      "--format=csv,noheader,nounits"], capture_output=True, text=True, timeout=10)
+                rows = [r.strip().split(", ") for r in out.stdout.splitlines() if r.strip()]
+            except Exception:
+                return None
+        sm = [float(r[1]) for r in rows if len(r) > 8 and r[1].replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in rows if len(r) > 8 and r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in rows:
+            if len(r) > 8:
+                for k, nm in enumerate(names):
+                    if r[5 + k].strip().lower() == "active":
+                        reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(rows)}
+
+
+# ---------------------------------------------------------------------------------------------
+def cpu_oracle_sample(cnf, B_sample, seed, target_s, max_steps=None):
+    """Times the FP64 oracle (as it stands) on B_sample candidates of the workload.
+    Returns (evals_per_s, seconds, steps, threads)."""
+    import oracle
+    from paper_2603_28796_b300 import synth
+
+    n = cnf.n_vars
+    d = synth.init_delta(n, B_sample, seed).astype(np.float64)
+    m = np.zeros_like(d)
+    v = np.zeros_like(d)
+    x = oracle.relax(d)
+
+    def one(t, d, m, v, x):
+        oracle.forward(n, cnf.clause_ptr, cnf.lits, x)
+        g, _ = oracle.backward(n, cnf.clause_ptr, cnf.lits, x)
+        d, m, v, x = oracle.adam(d, m, v, g, t)
+        oracle.round_check(n, cnf.clause_ptr, cnf.lits, d)
+        return d, m, v, x
+
+    t0 = time.perf_counter()
+    d, m, v, x = one(1, d, m, v, x)
+    t1 = time.perf_counter() - t0
+    steps = 1
+    if max_steps is None:
+        want = max(1, int(target_s / max(t1, 1e-3)))
+        extra = min(want - 1, 50)
+    else:
+        extra = max_steps - 1
+    t0 = time.perf_counter()
+    for t in range(2, 2 + extra):
+        d, m, v, x = one(t, d, m, v, x)
+    total = t1 + (time.perf_counter() - t0)
+    steps += extra
+    return cnf.nnz * B_sample * steps / total, total, steps, oracle.threads()
+
+
+# ---------------------------------------------------------------------------------------------
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    cnf, B, dtype, desc = workload_setup(args.workload, args.dtype)
+    B_sample = 16
+    import oracle
+
+    oracle.build()
+    # warm-up steps (untimed), then K timed oracle steps on the bounded sample
+    cpu_oracle_sample(cnf, B_sample, 1, 0, max_steps=max(1, args.warmup))
+    t0 = time.perf_counter()
+    evs, secs, steps, cores = cpu_oracle_sample(cnf, B_sample, 2, 0, max_steps=max(1, args.steps))
+    wall = time.perf_counter() - t0
+    sample = "%d of %d candidates per step, %d steps, FP64 oracle (forward, backward, Adam, round+check)" % (
+        B_sample, B, steps)
+    line = {
+        "impl": "reference", "metric": "fwd+bwd clause-literal evals/s", "value": evs, "unit": "evals/s",
+        "n_gpus": args.gpus, "steps": steps, "warmup": args.warmup, "ms_per_step": 1000.0 * secs / steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": desc, "B_sample": B_sample, "nnz": cnf.nnz, "n": cnf.n_vars, "m": cnf.n_clauses},
+        "cpu_baseline": {"value": evs, "unit": "evals/s", "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": evs, "unit": "evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "wall_s": wall,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_native(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2603_28796_b300 import _abi, synth
+    from paper_2603_28796_b300.engine import Engine
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local if world > 1 else 0)
+    torch.cuda.set_device(dev)
+
+    cnf, B, dtype, desc = workload_setup(args.workload, args.dtype)
+    prob = _abi.gs_load_cnf(cnf.n_vars, cnf.clause_ptr, cnf.lits)
+    info = prob.info()
+    eng = Engine(prob, B, dtype, seed=1000 * rank + 1)
+    nnz, n = cnf.nnz, cnf.n_vars
+    evals_per_step = nnz * B
+    s_bytes = {"f32": 4, "bf16": 2, "f16": 2}[dtype]
+
+    for _ in range(max(3, args.warmup)):
+        eng.step()
+    torch.cuda.synchronize()
+
+    K = args.steps
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(K)]
+    sampler = ClockSampler(dev.index if dev.index is not None else 0)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    t_start.record()
+    for k in range(K):
+        e0, e1, e2 = ev[k]
+        eng.t += 1
+        e0.record()
+        _abi.gs_step(prob, eng.delta, eng.m, eng.v, eng.t, x_in=eng.x[eng.cur], x_out=eng.x[eng.cur ^ 1],
+                     loss=eng.loss, bits=eng.bits)
+        e1.record()
+        eng.cur ^= 1
+        _abi.gs_check_bits(prob, eng.bits, B, eng.unsat, eng.best)
+        e2.record()
+    t_end.record()
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    if world > 1:
+        dist.barrier()
+    total_ms = t_start.elapsed_time(t_end)
+    step_ms = [ev[k][0].elapsed_time(ev[k][1]) for k in range(K)]
+    check_ms = [ev[k][1].elapsed_time(ev[k][2]) for k in range(K)]
+    if world > 1:
+        tt = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        total_ms = float(tt.item())
+    _abi.gs_sync_status(prob)
+
+    value = evals_per_step * K * world / (total_ms / 1000.0)
+    # roofline of the dominant kernel (fused variable-major pass inside gs_step)
+    peak, peak_kind = measured_peaks()
+    n_chunks = -(-B // (32 * (16 // s_bytes)))
+    compulsory = n * B * (24 + 2 * s_bytes) + n * ((B + 63) // 64) * 8 + n_chunks * 4 * (
+        info["n_occ_codes"] + info["n_var_tiles"] * 16)
+    gather_model = nnz * B * 2 * s_bytes + n * B * (24 + s_bytes)
+    mean_step_s = statistics.mean(step_ms) / 1000.0
+    achieved = compulsory / mean_step_s / 1e9
+    traffic = None
+    try:
+        with open(os.path.join(ROOT, "profiles", "var_pass_traffic.json")) as f:
+            tr = json.load(f)
+        if tr.get("workload") == args.workload and tr.get("B") == B and tr.get("dtype") == dtype:
+            traffic = tr.get("bytes_per_launch")
+    except Exception:
+        traffic = None
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": traffic, "peak_source": peak_kind,
+                "kernel": "k_var_pass (fused gradient+Adam+relax+round+loss credit), timed as the gs_step call",
+                "model": "compulsory bytes: n*B*(24+2s) state/value streams + bits + occurrence codes per chunk",
+                "bytes_per_launch": compulsory, "gather_model_bytes": gather_model,
+                "gather_model_GBps": gather_model / mean_step_s / 1e9,
+                "gather_model_frac": gather_model / mean_step_s / 1e9 / peak,
+                "gs_step_ms": statistics.mean(step_ms), "check_ms": statistics.mean(check_ms)}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        evs, secs, steps, cores = cpu_oracle_sample(cnf, 16, 7, args.cpu_seconds)
+        cpu = {"value": evs, "unit": "evals/s", "cores": cores, "kind": "oracle",
+               "sample": "16 of %d candidates, %d oracle steps (forward, backward, Adam, round+check), %.1f s" % (
+                   B, steps, secs)}
+
+    e2e = None
+    if not args.no_e2e:
+        # End to end through the public API with host buffers: every step copies that step's
+        # candidate logits from pinned host memory to the device, runs the step and the check,
+        # and reads back the per-candidate loss and unsat counts into pinned host memory.
+        Ke = max(3, min(K, 20))
+        host_delta = torch.from_numpy(synth.init_delta(n, B, seed=77 + rank)).pin_memory()
+        host_loss = torch.empty((1, B), dtype=torch.float64).pin_memory()
+        host_unsat = torch.empty((1, B), dtype=torch.int32).pin_memory()
+        torch.cuda.synchronize()
+        a0 = torch.cuda.Event(enable_timing=True)
+        a1 = torch.cuda.Event(enable_timing=True)
+        a0.record()
+        for _ in range(Ke):
+            eng.delta.copy_(host_delta[:, :B], non_blocking=True)
+            eng.step()
+            host_loss.copy_(eng.loss, non_blocking=True)
+            host_unsat.copy_(eng.unsat, non_blocking=True)
+        a1.record()
+        torch.cuda.synchronize()
+        e_ms = a0.elapsed_time(a1)
+        if world > 1:
+            tt = torch.tensor([e_ms], device=dev)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            e_ms = float(tt.item())
+        e2e = {"value": evals_per_step * Ke * world / (e_ms / 1000.0), "unit": "evals/s",
+               "h2d_bytes_per_step": n * B * 4, "d2h_bytes_per_step": B * 8 + B * 4, "steps": Ke}
+
+    line = {
+        "metric": "fwd+bwd clause-literal evals/s", "value": value, "unit": "evals/s", "n_gpus": world, "steps": K,
+        "warmup": max(3, args.warmup), "ms_per_step": total_ms / K, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": dtype, "data": "synthetic",
+        "config": {"workload": desc, "n": n, "m": cnf.n_clauses, "nnz": nnz, "B": B, "global_batch": B * world,
+                   "parallelism": "dp%d (independent candidate batches)" % world,
+                   "l2": "inputs larger than L2: x %.0f MB + delta/m/v %.0f MB per step" % (
+                       n * B * s_bytes / 1e6, n * B * 12 / 1e6),
+                   "steps_per_s": 1000.0 * K / total_ms},
+        "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "gpu_launches": 4 * K,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_native(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,256 @@
+/*
+ * gs.h - C ABI of the GaloisSAT differentiable solving stage on B300 (sm_103a).
+ *
+ * Method (arXiv 2603.28796, Sec. "Differentiable SAT Formulation"): a CNF formula's clauses
+ * become polynomials C_t = 1 - prod_i (1 - s_i) over literal values s_i (Eq. 1, Eq. 2); each
+ * variable is relaxed to x = sigma(delta / tau), delta being the difference of the two logits of
+ * the two Boolean states (Eq. 3 without noise); the loss is the MaxSAT sum of Eq. 5, kept here
+ * in its non-negative form L_unsat = sum_t prod_i (1 - s_i) = m + L (same gradient, zero exactly
+ * at satisfying Boolean points); Adam updates delta (Sec. "Experiment Setup": Adam, lr 0.5 on
+ * the two logits == lr 1.0 on delta); rounding is the argmax of Eq. 4, x_hat = [delta > 0].
+ *
+ * Conventions shared by every call below.
+ *  - Variables and candidates. A problem has n variables (summed over its instances). A batch
+ *    of B candidate assignments is stored var-major: element (v, b) of an array with row
+ *    stride ldB is at index v * ldB + b. ldB >= B, and every row must start on a 16-byte
+ *    boundary: ldB a multiple of 4 for float arrays, of 8 for 16-bit relaxed values (the
+ *    float arrays used with them share that ldB). Columns [B, ldB) are never written.
+ *  - Memory. Pointers marked "device" are CUDA device pointers owned by the caller, 16-byte
+ *    aligned (8-byte for double arrays, 4-byte for int32 ones); "host" pointers are read during
+ *    the call only. The library owns only the problem's index structures and a workspace that
+ *    grows on demand (see gs_reserve).
+ *  - Streams. gs_stream is a cudaStream_t (NULL = legacy default stream). Every compute call
+ *    only enqueues work on the stream and returns; results are ready when the stream is.
+ *  - Errors. Invalid arguments are rejected before anything is enqueued and leave outputs
+ *    untouched. Errors raised on the device (a bounded wait that timed out) are sticky and are
+ *    reported by gs_sync_status. Nothing crosses the ABI as an exception.
+ *  - Determinism. No floating-point atomics are used: for a given problem, B, dtype and GPU,
+ *    every output is bitwise reproducible.
+ *  - Limits. Clause width <= 256 literals; n < 2^28 - 2 variables; B <= 2^30.
+ */
+#ifndef GALOISSAT_GS_H
+#define GALOISSAT_GS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    GS_OK = 0,
+    GS_ERR_INVALID_ARG = 1, /* bad pointer, size, stride, alignment, literal or instance map */
+    GS_ERR_PARSE = 2,       /* malformed DIMACS text */
+    GS_ERR_OOM = 3,         /* host or device allocation failed */
+    GS_ERR_CUDA = 4,        /* a CUDA runtime call or kernel launch failed (see gs_last_error) */
+    GS_ERR_UNSUPPORTED = 5, /* beyond the limits above */
+    GS_ERR_TIMEOUT = 6,     /* a bounded device-side wait gave up (from gs_sync_status) */
+    GS_ERR_STATE = 7        /* wrong device, or workspace growth requested during stream capture */
+} gs_status;
+
+/* Storage type of the relaxed values x (the arrays the clause products gather from). The
+ * logits delta and the Adam moments are always float32; products accumulate in float32. */
+typedef enum { GS_F32 = 0, GS_BF16 = 1, GS_F16 = 2 } gs_dtype;
+
+typedef void* gs_stream; /* cudaStream_t */
+typedef struct gs_problem gs_problem;
+
+/* Problem statistics (gs_info_get, gs_inspect_cnf). */
+typedef struct {
+    int64_t n_vars;       /* variables, all instances */
+    int64_t n_clauses;    /* clauses, all instances */
+    int64_t nnz;          /* literal occurrences */
+    int32_t n_inst;       /* instances (1 for gs_load_cnf) */
+    int32_t max_k;        /* widest clause */
+    int64_t n_empty;      /* empty clauses (always unsatisfied, U_t = 1) */
+    int64_t n_unit;       /* clauses with one literal */
+    int64_t n_taut;       /* clauses containing some x and NOT x (kept and evaluated as written) */
+    int64_t n_dup;        /* clauses repeating a literal (each copy is its own factor) */
+    int64_t n_occ_codes;  /* size of the variable-major occurrence lists */
+    int64_t n_fwd_tiles;  /* clause tiles (forward, check) */
+    int64_t n_var_tiles;  /* occurrence tiles (backward, fused step) */
+    int64_t n_split;      /* variables whose occurrences are split over several tiles */
+    int64_t device_bytes; /* index structures held on the device */
+} gs_info;
+
+/* Adam hyper-parameters on delta. Defaults (gs_adam_default): lr 1.0, beta1 0.9, beta2 0.999,
+ * eps 1e-8, tau 1.0 - PyTorch's Adam defaults with the paper's lr 0.5 carried over from the
+ * two logits (theta_1, theta_0) to their difference delta, and the paper's tau = 1. Given in
+ * double precision: 1 - beta and the bias corrections are formed in double on the host and
+ * rounded once to float32 for the kernels (as PyTorch does with its Python-float scalars). */
+typedef struct {
+    double lr, beta1, beta2, eps, tau;
+} gs_adam;
+
+/* Fills *out with the defaults above. */
+void gs_adam_default(gs_adam* out);
+
+/*
+ * gs_load_cnf - build a problem from one CNF in CSR form (Sec. "Differentiable SAT
+ * Formulation": the clause set the polynomials of Eq. 2 are taken over).
+ *   n_vars      variables, literals refer to 1..n_vars.
+ *   n_clauses   clauses m.
+ *   clause_ptr  host [m + 1], clause_ptr[0] = 0, non-decreasing; clause t holds
+ *               lits[clause_ptr[t] .. clause_ptr[t+1]).
+ *   lits        host [clause_ptr[m]], DIMACS literals: +v for x_v, -v for NOT x_v, 1 <= v <= n.
+ *   stream      stream used for the uploads (the call returns after they complete).
+ *   out         receives the problem handle (owned by the caller, freed with gs_free).
+ * Builds on the device the clause->literal CSR (clause tiles), its transpose var->occurrence
+ * lists (occurrence tiles; each occurrence lists the other literals of its clause), and the
+ * tile schedules. Empty, unit, tautological and duplicate-literal clauses are kept and
+ * evaluated literally. Errors: GS_ERR_INVALID_ARG (null pointer, negative size, non-monotone
+ * clause_ptr, literal 0 or out of range), GS_ERR_UNSUPPORTED (limits), GS_ERR_OOM, GS_ERR_CUDA.
+ */
+gs_status gs_load_cnf(int64_t n_vars, int64_t n_clauses, const int64_t* clause_ptr, const int32_t* lits,
+                      gs_stream stream, gs_problem** out);
+
+/*
+ * gs_load_batch - many independent instances in one problem (the paper's batched training of
+ * many candidates, extended to many formulas of uneven size in one launch).
+ *   n_inst         instances.
+ *   n_vars         host [n_inst], variables of each instance (literals are instance-local,
+ *                  1..n_vars[i]).
+ *   n_clauses      host [n_inst], clauses of each instance.
+ *   clause_ptr     host [sum n_clauses + 1], one CSR over the concatenated clauses.
+ *   lits           host [clause_ptr[end]], instance-local DIMACS literals.
+ * Instance i owns candidate rows [sum_{j<i} n_vars[j], + n_vars[i]) of every candidate array
+ * and row i of every per-instance output ([n_inst][B] losses and unsat counts, best[n_inst]).
+ * Tiles never cross instances. Errors as gs_load_cnf.
+ */
+gs_status gs_load_batch(int32_t n_inst, const int64_t* n_vars, const int64_t* n_clauses, const int64_t* clause_ptr,
+                        const int32_t* lits, gs_stream stream, gs_problem** out);
+
+/*
+ * gs_load_dimacs - gs_load_cnf from a DIMACS CNF text file (header "p cnf n m", clauses
+ * terminated by 0, comment lines starting with 'c'). Errors: GS_ERR_PARSE on malformed text or
+ * a clause count that disagrees with the header, then as gs_load_cnf.
+ */
+gs_status gs_load_dimacs(const char* path, gs_stream stream, gs_problem** out);
+
+/*
+ * gs_inspect_cnf - validate a CSR formula and compute its gs_info fields (no device work; the
+ * tile counts and device_bytes are those gs_load_cnf would build). Errors as gs_load_cnf.
+ */
+gs_status gs_inspect_cnf(int64_t n_vars, int64_t n_clauses, const int64_t* clause_ptr, const int32_t* lits,
+                         gs_info* out);
+
+/* gs_info_get - statistics of a loaded problem. GS_ERR_INVALID_ARG on null arguments. */
+gs_status gs_info_get(const gs_problem* prob, gs_info* out);
+
+/*
+ * gs_reserve - size the workspace for batches of B candidates stored as dtype, so that later
+ * calls with (B, dtype) allocate nothing (required before capturing them in a CUDA graph).
+ * Synchronous. Errors: GS_ERR_INVALID_ARG, GS_ERR_OOM.
+ */
+gs_status gs_reserve(gs_problem* prob, int32_t B, gs_dtype dtype);
+
+/*
+ * gs_relax - relaxed values x = sigma(delta / tau) (Eq. 3 with two states and no Gumbel
+ * noise), rounded to nearest-even when dtype is 16-bit.
+ *   delta  device float [n][ldB] (input).   x  device dtype [n][ldB] (output).
+ * Errors: GS_ERR_INVALID_ARG (null, alignment, ldB, tau <= 0).
+ */
+gs_status gs_relax(gs_problem* prob, const float* delta, void* x, gs_dtype dtype, int32_t B, int64_t ldB, float tau,
+                   gs_stream stream);
+
+/*
+ * gs_forward - per-candidate loss of Eq. 2 + Eq. 5 at relaxed values x:
+ *   loss[i][b] = sum over clauses t of instance i of prod_{literals of t} f, f = 1 - x_v for a
+ *   positive literal and x_v for a negated one (= m_i + L_paper, L_paper = -sum_t C_t).
+ *   x     device dtype [n][ldB] (input).   loss  device double [n_inst][B] (output).
+ * Clause products accumulate in float32 (compensated within a tile); tiles are summed in
+ * float64 in a fixed order. Errors: GS_ERR_INVALID_ARG, GS_ERR_STATE, GS_ERR_CUDA.
+ */
+gs_status gs_forward(gs_problem* prob, const void* x, gs_dtype dtype, int32_t B, int64_t ldB, double* loss,
+                     gs_stream stream);
+
+/*
+ * gs_backward - gradient of the loss above with respect to x (back-propagation through
+ * Eq. 2; the paper's dashed backward arrows):
+ *   grad[v][b] = w_b * sum over occurrences (t, i) of v of  sign_i * prod_{j in t, j != i} f_j,
+ *   sign_i = -1 for a positive literal, +1 for a negated one; the leave-one-out product is the
+ *   prefix product before i times the suffix product after i (exact at zeros, no division);
+ *   w_b = dloss[inst(v)][b], or 1 when dloss is NULL.
+ *   x      device dtype [n][ldB].   dloss  device double [n_inst][B] or NULL.
+ *   grad   device float [n][ldB] (output; every (v, b < B) is written).
+ * Each variable's gradient is gathered over its occurrence list (no atomics).
+ * Errors: GS_ERR_INVALID_ARG, GS_ERR_STATE, GS_ERR_CUDA.
+ */
+gs_status gs_backward(gs_problem* prob, const void* x, gs_dtype dtype, int32_t B, int64_t ldB, const double* dloss,
+                      float* grad, gs_stream stream);
+
+/*
+ * gs_step - one Adam step on delta (Sec. "Experiment Setup"), in place:
+ *   g = dL/dx * sigma(delta/tau) sigma(-delta/tau) / tau,  m = b1 m + (1-b1) g,
+ *   v = b2 v + (1-b2) g^2,  delta -= lr (m / (1-b1^t)) / (sqrt(v / (1-b2^t)) + eps),
+ *   x_out = sigma(delta / tau) (Eq. 3),  bits = [delta > 0] (Eq. 4).
+ *   delta, m, v  device float [n][ldB], read and written.
+ *   grad         device float [n][ldB] holding dL/dx, or NULL for the fused path: the
+ *                gradient is formed from x_in in registers (gs_backward's arithmetic), never
+ *                stored, and the update follows in the same kernel.
+ *   x_in         device dtype [n][ldB]: the relaxed values the fused gradient is taken at
+ *                (normally sigma(delta/tau) from the previous step); ignored when grad != NULL.
+ *   x_out        device dtype [n][ldB] (output); must not overlap x_in. May be NULL only
+ *                when grad != NULL.
+ *   step         1-based Adam step t (bias correction).
+ *   adam         hyper-parameters, NULL = defaults.
+ *   loss         fused path only: device double [n_inst][B] receiving the loss at x_in (each
+ *                clause's product is credited once, at its first literal), or NULL.
+ *   bits         device uint64 [n][ceil(B/64)] receiving the rounded new delta (bit b%64 of word
+ *                b/64 of row v is [delta > 0]; bits >= B are 0), or NULL.
+ * Errors: GS_ERR_INVALID_ARG (also loss != NULL with grad != NULL), GS_ERR_STATE, GS_ERR_CUDA.
+ */
+gs_status gs_step(gs_problem* prob, float* delta, float* m, float* v, const float* grad, const void* x_in, void* x_out,
+                  gs_dtype dtype, int32_t B, int64_t ldB, int64_t step, const gs_adam* adam, double* loss,
+                  uint64_t* bits, gs_stream stream);
+
+/*
+ * gs_round_check - round (Eq. 4: x_hat = [delta > 0], ties to 0) and check every clause exactly
+ * in integer arithmetic (Eq. 2 at Boolean points: C_t = 1 iff some literal is true).
+ *   delta  device float [n][ldB].
+ *   bits   device uint64 [n][ceil(B/64)] receiving x_hat, or NULL (library workspace).
+ *   unsat  device int32 [n_inst][B]: number of unsatisfied clauses of each candidate.
+ *   best   device int32 [n_inst]: lowest candidate with the fewest unsatisfied clauses, or NULL.
+ * Errors: GS_ERR_INVALID_ARG, GS_ERR_STATE, GS_ERR_CUDA.
+ */
+gs_status gs_round_check(gs_problem* prob, const float* delta, int32_t B, int64_t ldB, uint64_t* bits, int32_t* unsat,
+                         int32_t* best, gs_stream stream);
+
+/*
+ * gs_check_bits - the check half of gs_round_check on assignments already packed as above
+ * (e.g. by gs_step's bits output). bits is read-only. Errors as gs_round_check.
+ */
+gs_status gs_check_bits(gs_problem* prob, const uint64_t* bits, int32_t B, int32_t* unsat, int32_t* best,
+                        gs_stream stream);
+
+/*
+ * gs_wait_selftest - exercises the device-side failure path: one warp waits on a barrier phase
+ * that nothing completes, gives up after limit_us microseconds (1..1e7) and records
+ * GS_ERR_TIMEOUT in the problem's sticky status, exactly as a stalled tile copy would. No
+ * memory is touched and the context stays usable; the next gs_sync_status returns
+ * GS_ERR_TIMEOUT and clears it. Errors: GS_ERR_INVALID_ARG, GS_ERR_STATE, GS_ERR_CUDA.
+ */
+gs_status gs_wait_selftest(gs_problem* prob, uint32_t limit_us, gs_stream stream);
+
+/*
+ * gs_sync_status - waits for all work on the problem's device, then reports and clears the
+ * sticky device-side status: GS_ERR_TIMEOUT if a bounded wait gave up since the last call
+ * (the outputs of that call are incomplete), GS_ERR_CUDA on an asynchronous CUDA error, else
+ * GS_OK.
+ */
+gs_status gs_sync_status(gs_problem* prob);
+
+/* gs_free - releases the problem and its device memory (after synchronising). NULL is a no-op. */
+void gs_free(gs_problem* prob);
+
+/* gs_status_str - static description of a status code. */
+const char* gs_status_str(gs_status status);
+
+/* gs_last_error - thread-local text of the last error raised in this thread ("" if none). */
+const char* gs_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GALOISSAT_GS_H */

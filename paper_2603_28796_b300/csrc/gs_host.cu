@@ -1,0 +1,954 @@
+// Host side of the C ABI (include/gs.h): validation, the clause->literal and var->occurrence
+// tile builders, device upload, workspace, and dispatch to the kernels in gs_kernels.cu.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "gs.h"
+#include "gs_internal.h"
+
+using namespace gs;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+gs_status fail(gs_status st, const std::string& msg) {
+    g_last_error = msg;
+    return st;
+}
+
+gs_status cuda_fail(cudaError_t e, const char* what) {
+    return fail(GS_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define GS_CUDA(call, what)                                  \
+    do {                                                     \
+        cudaError_t e__ = (call);                            \
+        if (e__ != cudaSuccess) return cuda_fail(e__, what); \
+    } while (0)
+
+// ---------------------------------------------------------------------------------------------
+// Host image of the device structures.
+struct HostPlan {
+    int64_t n = 0, m = 0, nnz = 0;
+    int32_t n_inst = 0, max_k = 0;
+    int64_t n_empty = 0, n_unit = 0, n_taut = 0, n_dup = 0;
+    std::vector<int64_t> var_off, clause_off, inst_empty;
+    // clause tiles
+    std::vector<uint32_t> fcodes;
+    std::vector<uint16_t> fctab;
+    std::vector<FwdItem> fitems;
+    // occurrence tiles
+    std::vector<uint32_t> vcodes;
+    std::vector<uint16_t> vrecs;
+    std::vector<uint32_t> vtab;
+    std::vector<VarItem> vitems;
+    int32_t n_split = 0, n_split_rows = 0;
+    // per-instance tile lists (ascending tile ids)
+    std::vector<int32_t> f_iptr, f_list, v_iptr, v_list;
+};
+
+// Validation + statistics. Fills plan.{n, m, nnz, n_inst, max_k, stats, var_off, clause_off,
+// inst_empty}.
+gs_status validate(int32_t n_inst, const int64_t* n_vars, const int64_t* n_clauses, const int64_t* clause_ptr,
+                   const int32_t* lits, HostPlan& P) {
+    if (n_inst < 1) return fail(GS_ERR_INVALID_ARG, "n_inst must be >= 1");
+    if (!n_vars || !n_clauses || !clause_ptr) return fail(GS_ERR_INVALID_ARG, "null n_vars/n_clauses/clause_ptr");
+    P.n_inst = n_inst;
+    P.var_off.assign(n_inst + 1, 0);
+    P.clause_off.assign(n_inst + 1, 0);
+    P.inst_empty.assign(n_inst, 0);
+    for (int32_t i = 0; i < n_inst; ++i) {
+        if (n_vars[i] < 0 || n_clauses[i] < 0) return fail(GS_ERR_INVALID_ARG, "negative n_vars or n_clauses");
+        P.var_off[i + 1] = P.var_off[i] + n_vars[i];
+        P.clause_off[i + 1] = P.clause_off[i] + n_clauses[i];
+        if (P.var_off[i + 1] > kMaxVars) return fail(GS_ERR_UNSUPPORTED, "too many variables (limit 2^28 - 2)");
+        if (P.clause_off[i + 1] > (int64_t(1) << 40)) return fail(GS_ERR_UNSUPPORTED, "too many clauses");
+    }
+    P.n = P.var_off[n_inst];
+    P.m = P.clause_off[n_inst];
+    if (clause_ptr[0] != 0) return fail(GS_ERR_INVALID_ARG, "clause_ptr[0] must be 0");
+    for (int64_t t = 0; t < P.m; ++t) {
+        const int64_t k = clause_ptr[t + 1] - clause_ptr[t];
+        if (k < 0) return fail(GS_ERR_INVALID_ARG, "clause_ptr is decreasing at clause " + std::to_string(t));
+        if (k > kMaxClauseWidth)
+            return fail(GS_ERR_UNSUPPORTED, "clause " + std::to_string(t) + " has " + std::to_string(k) +
+                                                " literals (limit 256)");
+    }
+    P.nnz = clause_ptr[P.m];
+    if (P.nnz > 0 && !lits) return fail(GS_ERR_INVALID_ARG, "null lits");
+    std::vector<int32_t> tmp;
+    for (int32_t i = 0; i < n_inst; ++i) {
+        const int64_t nv = n_vars[i];
+        for (int64_t t = P.clause_off[i]; t < P.clause_off[i + 1]; ++t) {
+            const int64_t a = clause_ptr[t], b = clause_ptr[t + 1];
+            const int k = static_cast<int>(b - a);
+            P.max_k = std::max(P.max_k, k);
+            if (k == 0) {
+                P.n_empty++;
+                P.inst_empty[i]++;
+            }
+            if (k == 1) P.n_unit++;
+            for (int64_t j = a; j < b; ++j) {
+                const int64_t l = lits[j];
+                const int64_t av = l < 0 ? -l : l;
+                if (l == 0 || av > nv)
+                    return fail(GS_ERR_INVALID_ARG, "literal " + std::to_string(l) + " of clause " + std::to_string(t) +
+                                                        " outside 1.." + std::to_string(nv));
+            }
+            tmp.assign(lits + a, lits + b);
+            std::sort(tmp.begin(), tmp.end(), [](int32_t x, int32_t y) {
+                const int32_t ax = x < 0 ? -x : x, ay = y < 0 ? -y : y;
+                return ax != ay ? ax < ay : x < y;
+            });
+            bool dup = false, taut = false;
+            for (int j = 1; j < k; ++j) {
+                if (tmp[j] == tmp[j - 1]) dup = true;
+                if (tmp[j] == -tmp[j - 1]) taut = true;
+            }
+            P.n_dup += dup;
+            P.n_taut += taut;
+        }
+    }
+    return GS_OK;
+}
+
+inline int64_t lit_row(const HostPlan& P, int32_t inst, int32_t lit) {
+    return P.var_off[inst] + (lit < 0 ? -static_cast<int64_t>(lit) : lit) - 1;
+}
+
+// Clause tiles: consecutive whole clauses of one instance, <= kFwdCodes codes, <= kFwdClauses.
+void build_fwd(const int64_t* clause_ptr, const int32_t* lits, HostPlan& P) {
+    P.fcodes.reserve(P.nnz);
+    P.f_iptr.assign(P.n_inst + 1, 0);
+    for (int32_t inst = 0; inst < P.n_inst; ++inst) {
+        int64_t t = P.clause_off[inst];
+        const int64_t te = P.clause_off[inst + 1];
+        while (t < te) {
+            FwdItem it{};
+            it.code_base = static_cast<int64_t>(P.fcodes.size());
+            it.ctab_base = static_cast<int64_t>(P.fctab.size());
+            it.inst = inst;
+            int nc = 0, ncodes = 0;
+            while (t < te && nc < kFwdClauses) {
+                const int k = static_cast<int>(clause_ptr[t + 1] - clause_ptr[t]);
+                if (ncodes + k > kFwdCodes) break;
+                P.fctab.push_back(static_cast<uint16_t>(ncodes));
+                for (int i = 0; i < k; ++i) {
+                    const int32_t l = lits[clause_ptr[t] + i];
+                    uint32_t c = static_cast<uint32_t>(lit_row(P, inst, l)) << kFShift;
+                    if (l < 0) c |= kFNeg;
+                    if (i == k - 1) c |= kFEnd;
+                    P.fcodes.push_back(c);
+                }
+                ncodes += k;
+                ++nc;
+                ++t;
+            }
+            P.fctab.push_back(static_cast<uint16_t>(ncodes));
+            it.n_codes = ncodes;
+            it.n_clauses = nc;
+            P.fitems.push_back(it);
+        }
+        P.f_iptr[inst + 1] = static_cast<int32_t>(P.fitems.size());
+    }
+    P.f_list.resize(P.fitems.size());
+    for (size_t i = 0; i < P.fitems.size(); ++i) P.f_list[i] = static_cast<int32_t>(i);
+}
+
+// Occurrence tiles: the transpose of the clause CSR. Occurrence (t, i) of variable v emits the
+// other literals of clause t in clause order (prefix then suffix of position i).
+gs_status build_var(const int64_t* clause_ptr, const int32_t* lits, HostPlan& P) {
+    const int64_t n = P.n;
+    std::vector<int64_t> occ_ptr(n + 1, 0);
+    std::vector<int32_t> clause_inst(P.m);
+    for (int32_t inst = 0; inst < P.n_inst; ++inst)
+        for (int64_t t = P.clause_off[inst]; t < P.clause_off[inst + 1]; ++t) clause_inst[t] = inst;
+    for (int64_t t = 0; t < P.m; ++t)
+        for (int64_t j = clause_ptr[t]; j < clause_ptr[t + 1]; ++j) occ_ptr[lit_row(P, clause_inst[t], lits[j]) + 1]++;
+    for (int64_t v = 0; v < n; ++v) occ_ptr[v + 1] += occ_ptr[v];
+    // occurrence -> literal index j (clause order per variable, by construction)
+    std::vector<int64_t> occ_lit(P.nnz);
+    {
+        std::vector<int64_t> fill(occ_ptr.begin(), occ_ptr.end() - 1);
+        for (int64_t t = 0; t < P.m; ++t)
+            for (int64_t j = clause_ptr[t]; j < clause_ptr[t + 1]; ++j)
+                occ_lit[fill[lit_row(P, clause_inst[t], lits[j])]++] = j;
+    }
+    std::vector<int64_t> lit_clause(P.nnz);
+    for (int64_t t = 0; t < P.m; ++t)
+        for (int64_t j = clause_ptr[t]; j < clause_ptr[t + 1]; ++j) lit_clause[j] = t;
+
+    auto occ_codes = [&](int64_t o) -> int {
+        const int64_t t = lit_clause[occ_lit[o]];
+        const int k = static_cast<int>(clause_ptr[t + 1] - clause_ptr[t]);
+        return k > 1 ? k - 1 : 1;
+    };
+    auto emit_occ = [&](int64_t o) {
+        const int64_t j = occ_lit[o];
+        const int64_t t = lit_clause[j];
+        const int32_t inst = clause_inst[t];
+        const int64_t a = clause_ptr[t], b = clause_ptr[t + 1];
+        const int32_t own = lits[j];
+        uint32_t tail = kVEnd;
+        if (own < 0) tail |= kVSelfNeg;
+        if (j == a) tail |= kVCredit;
+        if (b - a == 1) {
+            P.vcodes.push_back((kVSentinel << kVShift) | tail);
+            return;
+        }
+        const int64_t last = (j == b - 1) ? b - 2 : b - 1;
+        for (int64_t q = a; q < b; ++q) {
+            if (q == j) continue;
+            const int32_t l = lits[q];
+            uint32_t c = static_cast<uint32_t>(lit_row(P, inst, l)) << kVShift;
+            if (l < 0) c |= kVNeg;
+            if (q == last) c |= tail;
+            P.vcodes.push_back(c);
+        }
+    };
+    auto note_kk = [](int& acc, int k) { acc = (acc == -1) ? k : (acc == k ? acc : 0); };
+
+    struct Pending {
+        VarItem it;
+        int64_t cost;   // codes of the whole split variable (ordering key)
+    };
+    std::vector<Pending> light, split;
+
+    for (int32_t inst = 0; inst < P.n_inst; ++inst) {
+        const int64_t ra = P.var_off[inst], rb = P.var_off[inst + 1];
+        VarItem cur{};
+        bool open = false;
+        int cur_kk = -1;   // -1: no occurrence yet; 0: mixed widths
+        auto open_item = [&](int64_t v0) {
+            cur = VarItem{};
+            cur.code_base = static_cast<int64_t>(P.vcodes.size());
+            cur.rec_base = static_cast<int64_t>(P.vrecs.size());
+            cur.vtab_base = static_cast<int64_t>(P.vtab.size());
+            cur.v0 = static_cast<int32_t>(v0);
+            cur.split = -1;
+            cur.inst = inst;
+            open = true;
+            cur_kk = -1;
+        };
+        auto close_item = [&]() {
+            if (!open) return;
+            P.vtab.push_back((static_cast<uint32_t>(cur.n_occ) << 16) | static_cast<uint32_t>(cur.n_codes));
+            P.vrecs.push_back(static_cast<uint16_t>(cur.n_codes));
+            cur.kk = (cur_kk >= 1 && cur_kk <= 3) ? cur_kk : 0;
+            light.push_back({cur, 0});
+            open = false;
+        };
+        for (int64_t v = ra; v < rb; ++v) {
+            int64_t cost = 0;
+            for (int64_t o = occ_ptr[v]; o < occ_ptr[v + 1]; ++o) cost += occ_codes(o);
+            if (cost > kVarCodes) {
+                close_item();
+                // parts of <= kVarCodes codes, split at occurrence boundaries
+                std::vector<std::pair<int64_t, int64_t>> parts;
+                int64_t o = occ_ptr[v];
+                while (o < occ_ptr[v + 1]) {
+                    const int64_t o0 = o;
+                    int64_t c = 0;
+                    while (o < occ_ptr[v + 1] && c + occ_codes(o) <= kVarCodes) c += occ_codes(o++);
+                    parts.push_back({o0, o});
+                }
+                const int32_t slot = P.n_split++;
+                const int32_t row0 = P.n_split_rows;
+                P.n_split_rows += static_cast<int32_t>(parts.size());
+                for (size_t pi = 0; pi < parts.size(); ++pi) {
+                    VarItem it{};
+                    it.code_base = static_cast<int64_t>(P.vcodes.size());
+                    it.rec_base = static_cast<int64_t>(P.vrecs.size());
+                    it.vtab_base = static_cast<int64_t>(P.vtab.size());
+                    it.v0 = static_cast<int32_t>(v);
+                    it.nv = 1;
+                    it.split = slot;
+                    it.part = static_cast<int32_t>(pi);
+                    it.n_parts = static_cast<int32_t>(parts.size());
+                    it.split_row = row0;
+                    it.inst = inst;
+                    P.vtab.push_back(0u);
+                    int part_kk = -1;
+                    for (int64_t q = parts[pi].first; q < parts[pi].second; ++q) {
+                        P.vrecs.push_back(static_cast<uint16_t>(P.vcodes.size() - it.code_base));
+                        note_kk(part_kk, occ_codes(q));
+                        emit_occ(q);
+                        it.n_occ++;
+                    }
+                    it.kk = (part_kk >= 1 && part_kk <= 3) ? part_kk : 0;
+                    it.n_codes = static_cast<int32_t>(P.vcodes.size() - it.code_base);
+                    P.vrecs.push_back(static_cast<uint16_t>(it.n_codes));
+                    P.vtab.push_back((static_cast<uint32_t>(it.n_occ) << 16) | static_cast<uint32_t>(it.n_codes));
+                    split.push_back({it, cost});
+                }
+                continue;
+            }
+            if (open && (cur.nv == kVarVars || cur.n_codes + cost > kVarCodes)) close_item();
+            if (!open) open_item(v);
+            P.vtab.push_back((static_cast<uint32_t>(cur.n_occ) << 16) | static_cast<uint32_t>(cur.n_codes));
+            for (int64_t o = occ_ptr[v]; o < occ_ptr[v + 1]; ++o) {
+                P.vrecs.push_back(static_cast<uint16_t>(P.vcodes.size() - cur.code_base));
+                note_kk(cur_kk, occ_codes(o));
+                emit_occ(o);
+                cur.n_occ++;
+            }
+            cur.n_codes = static_cast<int32_t>(P.vcodes.size() - cur.code_base);
+            cur.nv++;
+        }
+        close_item();
+    }
+    // Schedule: parts of split variables first, largest variable first (they finish last
+    // otherwise), then whole-variable tiles in variable order.
+    std::stable_sort(split.begin(), split.end(), [](const Pending& a, const Pending& b) { return a.cost > b.cost; });
+    P.vitems.clear();
+    P.vitems.reserve(split.size() + light.size());
+    for (auto& s : split) P.vitems.push_back(s.it);
+    for (auto& l : light) P.vitems.push_back(l.it);
+    // per-instance lists, ascending tile id
+    std::vector<int32_t> cnt(P.n_inst + 1, 0);
+    for (auto& it : P.vitems) cnt[it.inst + 1]++;
+    for (int32_t i = 0; i < P.n_inst; ++i) cnt[i + 1] += cnt[i];
+    P.v_iptr = cnt;
+    P.v_list.resize(P.vitems.size());
+    std::vector<int32_t> fill(cnt.begin(), cnt.end() - 1);
+    for (size_t k = 0; k < P.vitems.size(); ++k) P.v_list[fill[P.vitems[k].inst]++] = static_cast<int32_t>(k);
+    return GS_OK;
+}
+
+template <typename T>
+gs_status upload(const std::vector<T>& h, T** d, int64_t* bytes, cudaStream_t s) {
+    // +64 B of zero padding: 16-byte bulk copies may round a tile's range up past the end.
+    const size_t nb = h.size() * sizeof(T) + 64;
+    void* p = nullptr;
+    if (cudaMalloc(&p, nb) != cudaSuccess) return fail(GS_ERR_OOM, "cudaMalloc of index structures failed");
+    *d = static_cast<T*>(p);
+    *bytes += static_cast<int64_t>(nb);
+    GS_CUDA(cudaMemsetAsync(p, 0, nb, s), "cudaMemsetAsync");
+    if (!h.empty()) GS_CUDA(cudaMemcpyAsync(p, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice, s), "upload");
+    return GS_OK;
+}
+
+Chunking chunking_for(int dtype, int32_t B) {
+    Chunking c{};
+    c.vec = (dtype == kF32) ? 4 : 8;
+    const int need = (B + c.vec - 1) / c.vec;
+    c.lc = 4;
+    while (c.lc < need && c.lc < 32) c.lc *= 2;
+    c.bc = c.lc * c.vec;
+    c.n_chunks = (B + c.bc - 1) / c.bc;
+    if (c.n_chunks < 1) c.n_chunks = 1;
+    c.bpad = c.n_chunks * c.bc;
+    return c;
+}
+
+inline int32_t nwords(int32_t B) { return (B + 63) / 64; }
+
+}  // namespace
+
+// =============================================================================================
+struct gs_problem {
+    int device = 0;
+    HostPlan h;   // statistics, offsets and per-instance lists (index arrays are released)
+    int64_t device_bytes = 0;
+    uint32_t* fcodes = nullptr;
+    uint16_t* fctab = nullptr;
+    FwdItem* fitems = nullptr;
+    uint32_t* vcodes = nullptr;
+    uint16_t* vrecs = nullptr;
+    uint32_t* vtab = nullptr;
+    VarItem* vitems = nullptr;
+    int32_t* f_iptr = nullptr;
+    int32_t* f_list = nullptr;
+    int32_t* v_iptr = nullptr;
+    int32_t* v_list = nullptr;
+    int64_t* inst_empty = nullptr;
+    int32_t n_fitems = 0, n_vitems = 0;
+    int64_t n_vcodes = 0;
+    int32_t* status = nullptr;   // sticky device status word
+    // workspace
+    int32_t* ctl = nullptr;      // [0] var head, [1] fwd head, [2] check head, [3] pad, [4..] split counters
+    size_t ctl_cap = 0;          // ints
+    float* part = nullptr;
+    size_t part_cap = 0;         // floats
+    float* split = nullptr;
+    size_t split_cap = 0;
+    uint64_t* bits = nullptr;
+    size_t bits_cap = 0;         // words
+};
+
+namespace {
+
+gs_status check_device(const gs_problem* p) {
+    int dev = -1;
+    GS_CUDA(cudaGetDevice(&dev), "cudaGetDevice");
+    if (dev != p->device) return fail(GS_ERR_STATE, "current CUDA device differs from the problem's device");
+    return GS_OK;
+}
+
+bool capturing(cudaStream_t s) {
+    cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &st) != cudaSuccess) return false;
+    return st != cudaStreamCaptureStatusNone;
+}
+
+template <typename T>
+gs_status grow(T** ptr, size_t* cap, size_t need, cudaStream_t s, bool in_capture, const char* what) {
+    if (need <= *cap) return GS_OK;
+    if (in_capture)
+        return fail(GS_ERR_STATE, std::string("workspace '") + what +
+                                      "' must grow during stream capture; call gs_reserve first");
+    if (*ptr) {
+        GS_CUDA(cudaStreamSynchronize(s), "cudaStreamSynchronize");
+        cudaFree(*ptr);
+        *ptr = nullptr;
+        *cap = 0;
+    }
+    void* p = nullptr;
+    if (cudaMalloc(&p, need * sizeof(T)) != cudaSuccess) return fail(GS_ERR_OOM, std::string("workspace ") + what);
+    *ptr = static_cast<T*>(p);
+    *cap = need;
+    return GS_OK;
+}
+
+gs_status ensure_ws(gs_problem* p, int dtype, int32_t B, bool need_bits, cudaStream_t s) {
+    const bool cap = capturing(s);
+    const Chunking c = chunking_for(dtype, B);
+    const size_t items = static_cast<size_t>(std::max(p->n_fitems, p->n_vitems));
+    gs_status st;
+    if ((st = grow(&p->part, &p->part_cap, std::max<size_t>(1, items * c.bpad), s, cap, "loss partials")) != GS_OK)
+        return st;
+    if ((st = grow(&p->split, &p->split_cap, std::max<size_t>(1, static_cast<size_t>(p->h.n_split_rows) * c.bpad), s,
+                   cap, "split partials")) != GS_OK)
+        return st;
+    if ((st = grow(&p->ctl, &p->ctl_cap, 4 + static_cast<size_t>(p->h.n_split) * c.n_chunks, s, cap, "counters")) !=
+        GS_OK)
+        return st;
+    if (need_bits) {
+        if ((st = grow(&p->bits, &p->bits_cap, std::max<size_t>(1, static_cast<size_t>(p->h.n) * nwords(B)), s, cap,
+                       "bits")) != GS_OK)
+            return st;
+    }
+    return GS_OK;
+}
+
+bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+gs_status check_batch(const gs_problem* p, int dtype, int32_t B, int64_t ldB) {
+    if (dtype < kF32 || dtype > kF16) return fail(GS_ERR_INVALID_ARG, "unknown dtype");
+    if (B < 0 || B > (1 << 30)) return fail(GS_ERR_INVALID_ARG, "B out of range");
+    if (ldB < B) return fail(GS_ERR_INVALID_ARG, "ldB < B");
+    const int vec = (dtype == kF32) ? 4 : 8;
+    if (ldB % vec != 0)
+        return fail(GS_ERR_INVALID_ARG, "ldB must be a multiple of 4 (float) / 8 (16-bit) elements");
+    if (p->h.n > 0 && ldB > (int64_t(1) << 40) / p->h.n) return fail(GS_ERR_INVALID_ARG, "ldB too large");
+    return GS_OK;
+}
+
+gs_status need_ptr(const void* ptr, const char* name, bool required = true) {
+    if (!ptr) return required ? fail(GS_ERR_INVALID_ARG, std::string("null ") + name) : GS_OK;
+    if (!aligned16(ptr)) return fail(GS_ERR_INVALID_ARG, std::string(name) + " is not 16-byte aligned");
+    return GS_OK;
+}
+
+AdamK adam_consts(const gs_adam& a, int64_t t) {
+    AdamK k{};
+    const double bc1 = 1.0 - std::pow(a.beta1, static_cast<double>(t));
+    const double bc2 = 1.0 - std::pow(a.beta2, static_cast<double>(t));
+    k.step_size = static_cast<float>(a.lr / bc1);
+    k.beta1 = static_cast<float>(a.beta1);
+    k.one_minus_beta1 = static_cast<float>(1.0 - a.beta1);
+    k.beta2 = static_cast<float>(a.beta2);
+    k.one_minus_beta2 = static_cast<float>(1.0 - a.beta2);
+    k.inv_sqrt_bc2 = static_cast<float>(1.0 / std::sqrt(bc2));
+    k.eps = static_cast<float>(a.eps);
+    k.inv_tau = static_cast<float>(1.0 / a.tau);
+    return k;
+}
+
+gs_status build(int32_t n_inst, const int64_t* n_vars, const int64_t* n_clauses, const int64_t* clause_ptr,
+                const int32_t* lits, HostPlan& P) {
+    gs_status st = validate(n_inst, n_vars, n_clauses, clause_ptr, lits, P);
+    if (st != GS_OK) return st;
+    try {
+        build_fwd(clause_ptr, lits, P);
+        st = build_var(clause_ptr, lits, P);
+    } catch (const std::bad_alloc&) {
+        return fail(GS_ERR_OOM, "host allocation failed while building tiles");
+    }
+    return st;
+}
+
+gs_status load(int32_t n_inst, const int64_t* n_vars, const int64_t* n_clauses, const int64_t* clause_ptr,
+               const int32_t* lits, gs_stream stream, gs_problem** out) {
+    if (!out) return fail(GS_ERR_INVALID_ARG, "null out");
+    *out = nullptr;
+    gs_problem* p = new (std::nothrow) gs_problem();
+    if (!p) return fail(GS_ERR_OOM, "host allocation");
+    gs_status st = build(n_inst, n_vars, n_clauses, clause_ptr, lits, p->h);
+    if (st != GS_OK) {
+        delete p;
+        return st;
+    }
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaGetDevice(&p->device);
+    if (e != cudaSuccess) {
+        delete p;
+        return cuda_fail(e, "cudaGetDevice");
+    }
+    HostPlan& H = p->h;
+    p->n_fitems = static_cast<int32_t>(H.fitems.size());
+    p->n_vitems = static_cast<int32_t>(H.vitems.size());
+    p->n_vcodes = static_cast<int64_t>(H.vcodes.size());
+    int64_t& db = p->device_bytes;
+    if ((st = upload(H.fcodes, &p->fcodes, &db, s)) != GS_OK || (st = upload(H.fctab, &p->fctab, &db, s)) != GS_OK ||
+        (st = upload(H.fitems, &p->fitems, &db, s)) != GS_OK || (st = upload(H.vcodes, &p->vcodes, &db, s)) != GS_OK ||
+        (st = upload(H.vrecs, &p->vrecs, &db, s)) != GS_OK || (st = upload(H.vtab, &p->vtab, &db, s)) != GS_OK ||
+        (st = upload(H.vitems, &p->vitems, &db, s)) != GS_OK || (st = upload(H.f_iptr, &p->f_iptr, &db, s)) != GS_OK ||
+        (st = upload(H.f_list, &p->f_list, &db, s)) != GS_OK || (st = upload(H.v_iptr, &p->v_iptr, &db, s)) != GS_OK ||
+        (st = upload(H.v_list, &p->v_list, &db, s)) != GS_OK ||
+        (st = upload(H.inst_empty, &p->inst_empty, &db, s)) != GS_OK) {
+        gs_free(p);
+        return st;
+    }
+    std::vector<int32_t> zero(1, 0);
+    if ((st = upload(zero, &p->status, &db, s)) != GS_OK) {
+        gs_free(p);
+        return st;
+    }
+    e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+        gs_free(p);
+        return cuda_fail(e, "upload synchronize");
+    }
+    // index arrays now live on the device only
+    std::vector<uint32_t>().swap(H.fcodes);
+    std::vector<uint16_t>().swap(H.fctab);
+    std::vector<FwdItem>().swap(H.fitems);
+    std::vector<uint32_t>().swap(H.vcodes);
+    std::vector<uint16_t>().swap(H.vrecs);
+    std::vector<uint32_t>().swap(H.vtab);
+    std::vector<VarItem>().swap(H.vitems);
+    *out = p;
+    return GS_OK;
+}
+
+void fill_info(const HostPlan& H, int64_t fitems, int64_t vitems, int64_t vcodes, int64_t dev_bytes, gs_info* o) {
+    std::memset(o, 0, sizeof(*o));
+    o->n_vars = H.n;
+    o->n_clauses = H.m;
+    o->nnz = H.nnz;
+    o->n_inst = H.n_inst;
+    o->max_k = H.max_k;
+    o->n_empty = H.n_empty;
+    o->n_unit = H.n_unit;
+    o->n_taut = H.n_taut;
+    o->n_dup = H.n_dup;
+    o->n_occ_codes = vcodes;
+    o->n_fwd_tiles = fitems;
+    o->n_var_tiles = vitems;
+    o->n_split = H.n_split;
+    o->device_bytes = dev_bytes;
+}
+
+int lanes_for_words(int32_t nwd) {
+    int lw = 1;
+    while (lw < nwd && lw < 32) lw *= 2;
+    return lw;
+}
+
+gs_status launch_check_all(gs_problem* p, const uint64_t* bits, int32_t B, int32_t* unsat, int32_t* best,
+                           cudaStream_t s) {
+    const int32_t nwd = nwords(B);
+    const int lw = lanes_for_words(nwd);
+    CheckParams cp{};
+    cp.items = p->fitems;
+    cp.n_items = p->n_fitems;
+    cp.n_wchunks = (nwd + lw - 1) / lw;
+    cp.B = B;
+    cp.nwd = nwd;
+    cp.codes = p->fcodes;
+    cp.ctab = p->fctab;
+    cp.bits = bits;
+    cp.unsat = unsat;
+    cp.head = p->ctl + 2;
+    cp.status = p->status;
+    GS_CUDA(cudaMemsetAsync(unsat, 0, sizeof(int32_t) * static_cast<size_t>(p->h.n_inst) * B, s), "memset unsat");
+    GS_CUDA(cudaMemsetAsync(p->ctl + 2, 0, sizeof(int32_t), s), "memset head");
+    const int64_t total = static_cast<int64_t>(cp.n_items) * cp.n_wchunks;
+    if (total > 0 && B > 0) {
+        const int grid = static_cast<int>(std::min<int64_t>(grid_check(lw), total));
+        GS_CUDA(launch_check(cp, lw, grid, s), "check kernel launch");
+    }
+    GS_CUDA(launch_finalize_check(unsat, p->inst_empty, p->h.n_inst, B, best, s), "finalize launch");
+    return GS_OK;
+}
+
+gs_status var_pass(gs_problem* p, int mode, const void* x_in, int dtype, int32_t B, int64_t ldB, const double* dloss,
+                   float* grad, float* delta, float* m, float* v, void* x_out, const AdamK* k, double* loss,
+                   uint64_t* bits, cudaStream_t s) {
+    gs_status st;
+    if ((st = ensure_ws(p, dtype, B, false, s)) != GS_OK) return st;
+    const Chunking c = chunking_for(dtype, B);
+    VarParams vp{};
+    vp.items = p->vitems;
+    vp.n_items = p->n_vitems;
+    vp.n_chunks = c.n_chunks;
+    vp.B = B;
+    vp.bpad = c.bpad;
+    vp.ldB = ldB;
+    vp.codes = p->vcodes;
+    vp.recs = p->vrecs;
+    vp.vtab = p->vtab;
+    vp.x_in = x_in;
+    vp.grad = grad;
+    vp.dloss = dloss;
+    vp.delta = delta;
+    vp.m = m;
+    vp.v = v;
+    vp.x_out = x_out;
+    vp.bits32 = reinterpret_cast<uint32_t*>(bits);
+    vp.nwd = nwords(B);
+    if (k) vp.adam = *k;
+    vp.loss_part = loss ? p->part : nullptr;
+    vp.split_part = p->split;
+    vp.split_cnt = p->ctl + 4;
+    vp.head = p->ctl;
+    vp.status = p->status;
+    GS_CUDA(cudaMemsetAsync(p->ctl, 0, sizeof(int32_t) * (4 + static_cast<size_t>(p->h.n_split) * c.n_chunks), s),
+            "memset counters");
+    const int64_t total = static_cast<int64_t>(vp.n_items) * c.n_chunks;
+    if (total > 0) {
+        const int grid = static_cast<int>(std::min<int64_t>(grid_var_pass(dtype, mode, c.lc), total));
+        GS_CUDA(launch_var_pass(vp, dtype, mode, c.lc, grid, s), "variable pass launch");
+    }
+    if (loss)
+        GS_CUDA(launch_loss_reduce(p->part, c.bpad, p->v_iptr, p->v_list, p->inst_empty, p->h.n_inst, B, loss, s),
+                "loss reduce launch");
+    return GS_OK;
+}
+
+}  // namespace
+
+// =============================================================================================
+extern "C" {
+
+void gs_adam_default(gs_adam* out) {
+    if (!out) return;
+    out->lr = 1.0;
+    out->beta1 = 0.9;
+    out->beta2 = 0.999;
+    out->eps = 1e-8;
+    out->tau = 1.0;
+}
+
+const char* gs_status_str(gs_status s) {
+    switch (s) {
+        case GS_OK: return "ok";
+        case GS_ERR_INVALID_ARG: return "invalid argument";
+        case GS_ERR_PARSE: return "malformed DIMACS input";
+        case GS_ERR_OOM: return "out of memory";
+        case GS_ERR_CUDA: return "CUDA error";
+        case GS_ERR_UNSUPPORTED: return "unsupported size";
+        case GS_ERR_TIMEOUT: return "device-side wait timed out";
+        case GS_ERR_STATE: return "invalid state";
+    }
+    return "unknown status";
+}
+
+const char* gs_last_error(void) { return g_last_error.c_str(); }
+
+gs_status gs_inspect_cnf(int64_t n_vars, int64_t n_clauses, const int64_t* clause_ptr, const int32_t* lits,
+                         gs_info* out) {
+    if (!out) return fail(GS_ERR_INVALID_ARG, "null out");
+    HostPlan P;
+    const gs_status st = build(1, &n_vars, &n_clauses, clause_ptr, lits, P);
+    if (st != GS_OK) return st;
+    int64_t bytes = 0;
+    bytes += (P.fcodes.size() * 4 + 64) + (P.fctab.size() * 2 + 64) + (P.fitems.size() * sizeof(FwdItem) + 64);
+    bytes += (P.vcodes.size() * 4 + 64) + (P.vrecs.size() * 2 + 64) + (P.vtab.size() * 4 + 64) +
+             (P.vitems.size() * sizeof(VarItem) + 64);
+    fill_info(P, static_cast<int64_t>(P.fitems.size()), static_cast<int64_t>(P.vitems.size()),
+              static_cast<int64_t>(P.vcodes.size()), bytes, out);
+    return GS_OK;
+}
+
+gs_status gs_load_cnf(int64_t n_vars, int64_t n_clauses, const int64_t* clause_ptr, const int32_t* lits,
+                      gs_stream stream, gs_problem** out) {
+    return load(1, &n_vars, &n_clauses, clause_ptr, lits, stream, out);
+}
+
+gs_status gs_load_batch(int32_t n_inst, const int64_t* n_vars, const int64_t* n_clauses, const int64_t* clause_ptr,
+                        const int32_t* lits, gs_stream stream, gs_problem** out) {
+    return load(n_inst, n_vars, n_clauses, clause_ptr, lits, stream, out);
+}
+
+gs_status gs_load_dimacs(const char* path, gs_stream stream, gs_problem** out) {
+    if (!path || !out) return fail(GS_ERR_INVALID_ARG, "null path/out");
+    FILE* f = std::fopen(path, "rb");
+    if (!f) return fail(GS_ERR_INVALID_ARG, std::string("cannot open ") + path);
+    std::string text;
+    {
+        char buf[1 << 16];
+        size_t got;
+        while ((got = std::fread(buf, 1, sizeof(buf), f)) > 0) text.append(buf, got);
+    }
+    std::fclose(f);
+    int64_t n = -1, m = -1;
+    std::vector<int64_t> cp(1, 0);
+    std::vector<int32_t> lits;
+    bool header = false, open_clause = false;
+    size_t pos = 0;
+    const size_t len = text.size();
+    while (pos < len) {
+        size_t eol = text.find('\n', pos);
+        if (eol == std::string::npos) eol = len;
+        size_t q = pos;
+        while (q < eol && (text[q] == ' ' || text[q] == '\t' || text[q] == '\r')) ++q;
+        if (q == eol || text[q] == 'c' || text[q] == '%') {
+            pos = eol + 1;
+            continue;
+        }
+        const std::string ln = text.substr(q, eol - q);
+        pos = eol + 1;
+        if (ln[0] == 'p') {
+            long long nn = -1, mm = -1;
+            if (header || std::sscanf(ln.c_str(), "p cnf %lld %lld", &nn, &mm) != 2 || nn < 0 || mm < 0)
+                return fail(GS_ERR_PARSE, "bad DIMACS header line");
+            n = nn;
+            m = mm;
+            header = true;
+            continue;
+        }
+        if (!header) return fail(GS_ERR_PARSE, "clause before the 'p cnf' header");
+        const char* c = ln.c_str();
+        while (*c) {
+            while (*c == ' ' || *c == '\t' || *c == '\r') ++c;
+            if (!*c) break;
+            char* end = nullptr;
+            const long long x = std::strtoll(c, &end, 10);
+            if (end == c || (*end && *end != ' ' && *end != '\t' && *end != '\r'))
+                return fail(GS_ERR_PARSE, std::string("unexpected token near '") + std::string(c).substr(0, 16) + "'");
+            c = end;
+            if (x == 0) {
+                cp.push_back(static_cast<int64_t>(lits.size()));
+                open_clause = false;
+            } else {
+                if (x > n || -x > n) return fail(GS_ERR_PARSE, "literal exceeds the header's variable count");
+                lits.push_back(static_cast<int32_t>(x));
+                open_clause = true;
+            }
+        }
+    }
+    if (!header) return fail(GS_ERR_PARSE, "missing 'p cnf' header");
+    if (open_clause) return fail(GS_ERR_PARSE, "last clause is not terminated by 0");
+    if (static_cast<int64_t>(cp.size()) - 1 != m) return fail(GS_ERR_PARSE, "clause count differs from the header");
+    return gs_load_cnf(n, m, cp.data(), lits.empty() ? nullptr : lits.data(), stream, out);
+}
+
+gs_status gs_info_get(const gs_problem* p, gs_info* out) {
+    if (!p || !out) return fail(GS_ERR_INVALID_ARG, "null argument");
+    fill_info(p->h, p->n_fitems, p->n_vitems, p->n_vcodes, p->device_bytes, out);
+    return GS_OK;
+}
+
+gs_status gs_reserve(gs_problem* p, int32_t B, gs_dtype dtype) {
+    if (!p) return fail(GS_ERR_INVALID_ARG, "null problem");
+    gs_status st = check_device(p);
+    if (st != GS_OK) return st;
+    if ((st = check_batch(p, dtype, B, ((B + 7) / 8) * 8)) != GS_OK) return st;
+    st = ensure_ws(p, dtype, B, true, nullptr);
+    if (st != GS_OK) return st;
+    // First use of a kernel instantiation queries its occupancy and sets its shared-memory
+    // attributes; do that here, outside any stream capture.
+    const Chunking c = chunking_for(dtype, B);
+    grid_var_pass(dtype, kModeGrad, c.lc);
+    grid_var_pass(dtype, kModeAdam, c.lc);
+    grid_forward(dtype, c.lc);
+    grid_check(lanes_for_words(nwords(B)));
+    GS_CUDA(cudaDeviceSynchronize(), "cudaDeviceSynchronize");
+    return GS_OK;
+}
+
+gs_status gs_relax(gs_problem* p, const float* delta, void* x, gs_dtype dtype, int32_t B, int64_t ldB, float tau,
+                   gs_stream stream) {
+    if (!p) return fail(GS_ERR_INVALID_ARG, "null problem");
+    gs_status st;
+    if ((st = check_batch(p, dtype, B, ldB)) != GS_OK) return st;
+    if (!(tau > 0.0f)) return fail(GS_ERR_INVALID_ARG, "tau must be > 0");
+    const bool any = p->h.n > 0 && B > 0;
+    if ((st = need_ptr(delta, "delta", any)) != GS_OK || (st = need_ptr(x, "x", any)) != GS_OK) return st;
+    if ((st = check_device(p)) != GS_OK) return st;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    GS_CUDA(launch_relax(delta, x, dtype, p->h.n, B, ldB, 1.0f / tau, s), "relax launch");
+    return GS_OK;
+}
+
+gs_status gs_forward(gs_problem* p, const void* x, gs_dtype dtype, int32_t B, int64_t ldB, double* loss,
+                     gs_stream stream) {
+    if (!p) return fail(GS_ERR_INVALID_ARG, "null problem");
+    gs_status st;
+    if ((st = check_batch(p, dtype, B, ldB)) != GS_OK) return st;
+    if ((st = need_ptr(x, "x", p->h.n > 0 && B > 0)) != GS_OK) return st;
+    if (B > 0 && !loss) return fail(GS_ERR_INVALID_ARG, "null loss");
+    if (loss && (reinterpret_cast<uintptr_t>(loss) & 7u)) return fail(GS_ERR_INVALID_ARG, "loss misaligned");
+    if ((st = check_device(p)) != GS_OK) return st;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (B == 0) return GS_OK;
+    if ((st = ensure_ws(p, dtype, B, false, s)) != GS_OK) return st;
+    const Chunking c = chunking_for(dtype, B);
+    FwdParams fp{};
+    fp.items = p->fitems;
+    fp.n_items = p->n_fitems;
+    fp.n_chunks = c.n_chunks;
+    fp.B = B;
+    fp.bpad = c.bpad;
+    fp.ldB = ldB;
+    fp.codes = p->fcodes;
+    fp.ctab = p->fctab;
+    fp.x = x;
+    fp.loss_part = p->part;
+    fp.head = p->ctl + 1;
+    fp.status = p->status;
+    GS_CUDA(cudaMemsetAsync(p->ctl + 1, 0, sizeof(int32_t), s), "memset head");
+    const int64_t total = static_cast<int64_t>(fp.n_items) * c.n_chunks;
+    if (total > 0) {
+        const int grid = static_cast<int>(std::min<int64_t>(grid_forward(dtype, c.lc), total));
+        GS_CUDA(launch_forward(fp, dtype, c.lc, grid, s), "forward launch");
+    }
+    GS_CUDA(launch_loss_reduce(p->part, c.bpad, p->f_iptr, p->f_list, p->inst_empty, p->h.n_inst, B, loss, s),
+            "loss reduce launch");
+    return GS_OK;
+}
+
+gs_status gs_backward(gs_problem* p, const void* x, gs_dtype dtype, int32_t B, int64_t ldB, const double* dloss,
+                      float* grad, gs_stream stream) {
+    if (!p) return fail(GS_ERR_INVALID_ARG, "null problem");
+    gs_status st;
+    if ((st = check_batch(p, dtype, B, ldB)) != GS_OK) return st;
+    const bool any = p->h.n > 0 && B > 0;
+    if ((st = need_ptr(x, "x", any)) != GS_OK || (st = need_ptr(grad, "grad", any)) != GS_OK) return st;
+    if (dloss && (reinterpret_cast<uintptr_t>(dloss) & 7u)) return fail(GS_ERR_INVALID_ARG, "dloss misaligned");
+    if ((st = check_device(p)) != GS_OK) return st;
+    if (!any) return GS_OK;
+    return var_pass(p, kModeGrad, x, dtype, B, ldB, dloss, grad, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr,
+                    nullptr, static_cast<cudaStream_t>(stream));
+}
+
+gs_status gs_step(gs_problem* p, float* delta, float* m, float* v, const float* grad, const void* x_in, void* x_out,
+                  gs_dtype dtype, int32_t B, int64_t ldB, int64_t step, const gs_adam* adam, double* loss,
+                  uint64_t* bits, gs_stream stream) {
+    if (!p) return fail(GS_ERR_INVALID_ARG, "null problem");
+    gs_status st;
+    if ((st = check_batch(p, dtype, B, ldB)) != GS_OK) return st;
+    if (step < 1) return fail(GS_ERR_INVALID_ARG, "step must be >= 1");
+    gs_adam a;
+    gs_adam_default(&a);
+    if (adam) a = *adam;
+    if (!(a.tau > 0.0) || !(a.lr >= 0.0) || !(a.eps >= 0.0) || !(a.beta1 >= 0.0 && a.beta1 < 1.0) ||
+        !(a.beta2 >= 0.0 && a.beta2 < 1.0))
+        return fail(GS_ERR_INVALID_ARG, "Adam hyper-parameters out of range");
+    const bool any = p->h.n > 0 && B > 0;
+    if ((st = need_ptr(delta, "delta", any)) != GS_OK || (st = need_ptr(m, "m", any)) != GS_OK ||
+        (st = need_ptr(v, "v", any)) != GS_OK || (st = need_ptr(x_out, "x_out", false)) != GS_OK ||
+        (st = need_ptr(bits, "bits", false)) != GS_OK)
+        return st;
+    if (grad) {
+        if ((st = need_ptr(grad, "grad")) != GS_OK) return st;
+        if (loss) return fail(GS_ERR_INVALID_ARG, "loss output is only produced by the fused path (grad == NULL)");
+    } else {
+        if ((st = need_ptr(x_in, "x_in", any)) != GS_OK) return st;
+        if (!x_out && any) return fail(GS_ERR_INVALID_ARG, "the fused step (grad == NULL) needs x_out");
+        if (x_in && x_in == x_out) return fail(GS_ERR_INVALID_ARG, "x_out must not alias x_in");
+        if (loss && (reinterpret_cast<uintptr_t>(loss) & 7u)) return fail(GS_ERR_INVALID_ARG, "loss misaligned");
+    }
+    if ((st = check_device(p)) != GS_OK) return st;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (!any) return GS_OK;
+    const AdamK k = adam_consts(a, step);
+    if (grad) {
+        GS_CUDA(launch_adam(delta, m, v, grad, x_out, dtype, p->h.n, B, ldB, k, s), "adam launch");
+        if (bits)
+            GS_CUDA(launch_round(delta, reinterpret_cast<uint32_t*>(bits), p->h.n, B, ldB, nwords(B), s),
+                    "round launch");
+        return GS_OK;
+    }
+    return var_pass(p, kModeAdam, x_in, dtype, B, ldB, nullptr, nullptr, delta, m, v, x_out, &k, loss, bits, s);
+}
+
+gs_status gs_round_check(gs_problem* p, const float* delta, int32_t B, int64_t ldB, uint64_t* bits, int32_t* unsat,
+                         int32_t* best, gs_stream stream) {
+    if (!p) return fail(GS_ERR_INVALID_ARG, "null problem");
+    gs_status st;
+    if ((st = check_batch(p, kF32, B, ldB)) != GS_OK) return st;
+    if ((st = need_ptr(delta, "delta", p->h.n > 0 && B > 0)) != GS_OK ||
+        (st = need_ptr(bits, "bits", false)) != GS_OK || (st = need_ptr(unsat, "unsat", B > 0)) != GS_OK)
+        return st;
+    if (best && (reinterpret_cast<uintptr_t>(best) & 3u)) return fail(GS_ERR_INVALID_ARG, "best misaligned");
+    if ((st = check_device(p)) != GS_OK) return st;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if ((st = ensure_ws(p, kF32, std::max(B, 1), bits == nullptr, s)) != GS_OK) return st;
+    uint64_t* b = bits ? bits : p->bits;
+    if (p->h.n > 0 && B > 0)
+        GS_CUDA(launch_round(delta, reinterpret_cast<uint32_t*>(b), p->h.n, B, ldB, nwords(B), s), "round launch");
+    return launch_check_all(p, b, B, unsat, best, s);
+}
+
+gs_status gs_check_bits(gs_problem* p, const uint64_t* bits, int32_t B, int32_t* unsat, int32_t* best,
+                        gs_stream stream) {
+    if (!p) return fail(GS_ERR_INVALID_ARG, "null problem");
+    if (B < 0 || B > (1 << 30)) return fail(GS_ERR_INVALID_ARG, "B out of range");
+    gs_status st;
+    if ((st = need_ptr(bits, "bits", p->h.n > 0 && B > 0)) != GS_OK || (st = need_ptr(unsat, "unsat", B > 0)) != GS_OK)
+        return st;
+    if (best && (reinterpret_cast<uintptr_t>(best) & 3u)) return fail(GS_ERR_INVALID_ARG, "best misaligned");
+    if ((st = check_device(p)) != GS_OK) return st;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if ((st = ensure_ws(p, kF32, std::max(B, 1), false, s)) != GS_OK) return st;
+    return launch_check_all(p, bits, B, unsat, best, s);
+}
+
+gs_status gs_wait_selftest(gs_problem* p, uint32_t limit_us, gs_stream stream) {
+    if (!p) return fail(GS_ERR_INVALID_ARG, "null problem");
+    if (limit_us == 0 || limit_us > 10000000u) return fail(GS_ERR_INVALID_ARG, "limit_us must be in 1..1e7");
+    gs_status st = check_device(p);
+    if (st != GS_OK) return st;
+    GS_CUDA(launch_wait_selftest(p->status, static_cast<uint64_t>(limit_us) * 1000ull, static_cast<cudaStream_t>(stream)),
+            "wait self-test launch");
+    return GS_OK;
+}
+
+gs_status gs_sync_status(gs_problem* p) {
+    if (!p) return fail(GS_ERR_INVALID_ARG, "null problem");
+    gs_status st = check_device(p);
+    if (st != GS_OK) return st;
+    GS_CUDA(cudaDeviceSynchronize(), "cudaDeviceSynchronize");
+    int32_t h = 0;
+    GS_CUDA(cudaMemcpy(&h, p->status, sizeof(h), cudaMemcpyDeviceToHost), "read status");
+    if (h) {
+        GS_CUDA(cudaMemset(p->status, 0, sizeof(int32_t)), "clear status");
+        if (h & kStatusTimeout) return fail(GS_ERR_TIMEOUT, "a bounded device-side wait timed out");
+    }
+    return GS_OK;
+}
+
+void gs_free(gs_problem* p) {
+    if (!p) return;
+    int dev = -1;
+    if (cudaGetDevice(&dev) == cudaSuccess && dev == p->device) cudaDeviceSynchronize();
+    void* ptrs[] = {p->fcodes, p->fctab,  p->fitems,     p->vcodes, p->vrecs, p->vtab, p->vitems, p->f_iptr, p->f_list,
+                    p->v_iptr, p->v_list, p->inst_empty, p->status, p->ctl,   p->part, p->split,  p->bits};
+    for (void* q : ptrs)
+        if (q) cudaFree(q);
+    delete p;
+}
+
+}  // extern "C"

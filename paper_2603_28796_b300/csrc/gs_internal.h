@@ -1,0 +1,191 @@
+// Internal layout shared by the host loader (gs_host.cu) and the kernels (gs_kernels.cu).
+// Not part of the public C ABI (include/gs.h).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace gs {
+
+// ---------------------------------------------------------------------------------------------
+// Limits of this implementation.
+constexpr int kMaxClauseWidth = 256;            // literals per clause (8-bit fields in the tiles)
+constexpr int64_t kMaxVars = (1LL << 28) - 2;   // 28-bit variable field in occurrence codes
+
+// Forward / check tiles (clause-major). A tile holds whole clauses.
+constexpr int kFwdCodes = 512;     // literal codes per tile
+constexpr int kFwdClauses = 256;   // clauses per tile
+// Occurrence tiles (variable-major). A tile holds whole variables, or one part of a variable
+// whose occurrence list alone exceeds kVarCodes.
+constexpr int kVarCodes = 384;     // occurrence codes per tile
+constexpr int kVarVars = 64;       // variables per tile
+
+constexpr int align16(int x) { return (x + 15) & ~15; }
+
+// Per-warp shared-memory staging buffer of one forward tile: clause offsets + codes.
+constexpr int kFwdCtabBytes = align16((kFwdClauses + 1) * 2 + 15);
+constexpr int kFwdCodeBytes = align16(kFwdCodes * 4 + 15);
+constexpr int kFwdBufBytes = kFwdCtabBytes + kFwdCodeBytes;
+// Per-warp staging buffer of one occurrence tile: var table + occurrence offsets + codes.
+constexpr int kVarVtabBytes = align16((kVarVars + 1) * 4 + 15);
+constexpr int kVarRecBytes = align16((kVarCodes + 1) * 2 + 15);
+constexpr int kVarCodeBytes = align16(kVarCodes * 4 + 15);
+constexpr int kVarBufBytes = kVarVtabBytes + kVarRecBytes + kVarCodeBytes;
+// Two buffers (double buffering) + two mbarriers per warp.
+constexpr int kFwdWarpBytes = 2 * kFwdBufBytes + 16;
+constexpr int kVarWarpBytes = 2 * kVarBufBytes + 16;
+
+constexpr int kWarps = 8;          // warps per CTA of the tiled kernels
+constexpr int kThreads = kWarps * 32;
+
+// ---------------------------------------------------------------------------------------------
+// Clause-major literal code (forward and check tiles), one uint32 per literal occurrence:
+//   bit 0     : negated literal
+//   bit 1     : last literal of its clause
+//   bits 2-31 : variable row (global, instance offset included)
+constexpr uint32_t kFNeg = 1u, kFEnd = 2u;
+constexpr int kFShift = 2;
+
+// Variable-major occurrence code. The occurrence (t, i) of variable v in clause t at position i
+// is stored as the list of the OTHER literals of clause t in clause order (positions < i, then
+// positions > i), one uint32 each; its leave-one-out product is the product of their factors,
+// i.e. the prefix product before i times the suffix product after i.
+//   bit 0     : this other literal is negated
+//   bit 1     : last code of the occurrence (the leave-one-out product is complete)
+//   bit 2     : (on the last code) the occurrence's own literal is negated
+//   bit 3     : (on the last code) the own literal is at position 0: this occurrence also
+//               carries the clause's forward value U_t = f_i * LOO_i (each clause exactly once)
+//   bits 4-31 : variable row of the other literal; kVSentinel for a unit clause (no other
+//               literal, factor 1, no load)
+constexpr uint32_t kVNeg = 1u, kVEnd = 2u, kVSelfNeg = 4u, kVCredit = 8u;
+constexpr int kVShift = 4;
+constexpr uint32_t kVSentinel = (1u << 28) - 1u;
+
+struct FwdItem {
+    int64_t code_base;   // first code of the tile in fcodes
+    int64_t ctab_base;   // first entry in fctab (n_clauses + 1 uint16 offsets, relative)
+    int32_t n_codes;
+    int32_t n_clauses;
+    int32_t inst;
+    int32_t pad;
+};
+static_assert(sizeof(FwdItem) == 32, "FwdItem layout");
+
+struct VarItem {
+    int64_t code_base;   // first code of the tile in vcodes
+    int64_t rec_base;    // first entry in vrecs (n_occ + 1 uint16 code offsets, relative)
+    int64_t vtab_base;   // first entry in vtab (nv + 1 entries: occ_rel << 16 | code_rel)
+    int32_t v0;          // first variable row
+    int32_t nv;          // variables (1 for a part of a split variable)
+    int32_t n_codes;
+    int32_t n_occ;
+    int32_t split;       // -1: whole variables; else the split variable's slot
+    int32_t part;        // part index within the split variable
+    int32_t n_parts;     // parts of the split variable
+    int32_t split_row;   // first scratch row of the split variable's parts
+    int32_t inst;
+    int32_t kk;          // every occurrence in the tile has exactly kk codes (1..3), or 0 (mixed)
+};
+static_assert(sizeof(VarItem) == 64, "VarItem layout");
+
+// Adam constants, prepared on the host in double precision.
+struct AdamK {
+    float step_size;      // lr / (1 - beta1^t)
+    float beta1, one_minus_beta1;
+    float beta2, one_minus_beta2;
+    float inv_sqrt_bc2;   // 1 / sqrt(1 - beta2^t)
+    float eps;
+    float inv_tau;
+};
+
+// Candidate chunking of a [n][ldB] array of element size s: each lane owns VEC = 16/s
+// consecutive candidates, LC lanes cover one chunk of Bc = LC * VEC candidates, and the
+// G = 32 / LC lane groups of a warp work on different occurrences / clauses of the same tile.
+struct Chunking {
+    int vec, lc, bc, n_chunks, bpad;
+};
+
+enum Mode { kModeGrad = 0, kModeAdam = 1 };
+enum Dtype { kF32 = 0, kBF16 = 1, kF16 = 2 };
+
+struct VarParams {
+    const VarItem* items;
+    int32_t n_items;
+    int32_t n_chunks;
+    int32_t B;
+    int32_t bpad;
+    int64_t ldB;
+    const uint32_t* codes;
+    const uint16_t* recs;
+    const uint32_t* vtab;
+    const void* x_in;
+    float* grad;             // kModeGrad
+    const double* dloss;     // kModeGrad, [n_inst][B] or null
+    float* delta;            // kModeAdam
+    float* m;
+    float* v;
+    void* x_out;
+    uint32_t* bits32;        // [n][2 * nwd] or null
+    int32_t nwd;
+    AdamK adam;
+    float* loss_part;        // [n_items][bpad] or null
+    float* split_part;       // [split rows][bpad]
+    int32_t* split_cnt;      // [n_split][n_chunks]
+    int32_t* head;
+    int32_t* status;
+};
+
+struct FwdParams {
+    const FwdItem* items;
+    int32_t n_items;
+    int32_t n_chunks;
+    int32_t B;
+    int32_t bpad;
+    int64_t ldB;
+    const uint32_t* codes;
+    const uint16_t* ctab;
+    const void* x;
+    float* loss_part;        // [n_items][bpad]
+    int32_t* head;
+    int32_t* status;
+};
+
+struct CheckParams {
+    const FwdItem* items;
+    int32_t n_items;
+    int32_t n_wchunks;       // word chunks of LW words
+    int32_t B;
+    int32_t nwd;             // uint64 words per row
+    const uint32_t* codes;
+    const uint16_t* ctab;
+    const uint64_t* bits;    // [n][nwd]
+    int32_t* unsat;          // [n_inst][B], accumulated with integer atomics
+    int32_t* head;
+    int32_t* status;
+};
+
+// Device status bits (sticky until read by gs_sync_status).
+constexpr int32_t kStatusTimeout = 1;
+
+// ---------------------------------------------------------------------------------------------
+// Launchers (gs_kernels.cu). They return cudaGetLastError() of the launch.
+cudaError_t launch_var_pass(const VarParams& p, int dtype, int mode, int lc, int grid, cudaStream_t s);
+cudaError_t launch_forward(const FwdParams& p, int dtype, int lc, int grid, cudaStream_t s);
+cudaError_t launch_check(const CheckParams& p, int lw, int grid, cudaStream_t s);
+cudaError_t launch_loss_reduce(const float* part, int32_t bpad, const int32_t* inst_items_ptr,
+                               const int32_t* inst_items, const int64_t* n_empty, int32_t n_inst,
+                               int32_t B, double* loss, cudaStream_t s);
+cudaError_t launch_finalize_check(int32_t* unsat, const int64_t* n_empty, int32_t n_inst, int32_t B,
+                                  int32_t* best, cudaStream_t s);
+cudaError_t launch_relax(const float* delta, void* x, int dtype, int64_t n, int32_t B, int64_t ldB,
+                         float inv_tau, cudaStream_t s);
+cudaError_t launch_round(const float* delta, uint32_t* bits32, int64_t n, int32_t B, int64_t ldB,
+                         int32_t nwd, cudaStream_t s);
+cudaError_t launch_adam(float* delta, float* m, float* v, const float* grad, void* x_out, int dtype,
+                        int64_t n, int32_t B, int64_t ldB, const AdamK& k, cudaStream_t s);
+cudaError_t launch_wait_selftest(int32_t* status, uint64_t limit_ns, cudaStream_t s);
+// Occupancy-derived persistent grid size for a tiled kernel instantiation.
+int grid_var_pass(int dtype, int mode, int lc);
+int grid_forward(int dtype, int lc);
+int grid_check(int lw);
+
+}  // namespace gs

@@ -1,0 +1,1280 @@
+// sm_103a kernels of the GaloisSAT differentiable solving stage (arXiv 2603.28796).
+//
+// Layout: every candidate array is var-major, row v = variable v, columns = candidates, row
+// stride ldB elements (16-byte rows). A lane owns VEC = 16 / sizeof(T) consecutive candidates
+// and reads them with one 16-byte load; LC lanes cover a chunk of Bc = LC * VEC candidates;
+// the G = 32 / LC lane groups of a warp work on different clauses / occurrences of one tile.
+// Work items (tiles x candidate chunks) come from an integer work queue in chunk-major order,
+// so that the rows of the current chunk stay resident in L2 while every tile gathers from it.
+// Each warp stages its tile's index data into its own shared-memory buffer with 1-D bulk TMA
+// (cp.async.bulk + mbarrier), double-buffered so the next tile loads while this one computes.
+//
+// No floating-point atomics: gradients are gathered per variable over the occurrence lists,
+// split variables are combined in a fixed order by the last part to finish (integer counter),
+// and loss partials are summed per tile in FP32 (Kahan) and across tiles in FP64 in tile order.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include <cstdint>
+
+#include "gs_internal.h"
+
+namespace gs {
+namespace {
+
+constexpr uint64_t kWaitNs = 2000000000ull;   // bounded mbarrier wait: 2 s, then error status
+
+// ------------------------------------------------------------------------------------------
+// PTX helpers: mbarrier + 1-D bulk copy global -> shared.
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void fence_proxy_async() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_addr(dst)),
+        "l"(__cvta_generic_to_global(src)), "r"(bytes), "r"(smem_addr(bar))
+        : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+// Wait for a phase of the mbarrier with a time limit (and an iteration limit, in case the
+// timer does not advance). Returns false on timeout.
+__device__ __noinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, uint64_t limit_ns) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = global_ns();
+    for (uint32_t it = 0; it < (1u << 26); ++it) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((it & 255u) == 0u && global_ns() - t0 > limit_ns) return false;
+    }
+    return false;
+}
+
+struct Span {
+    uintptr_t src;
+    uint32_t bytes;   // 16-byte multiple
+};
+// The 16-byte aligned superset [lo, hi) of [p, p + bytes); the device arrays carry 64 bytes of
+// padding so that hi never leaves the allocation.
+__device__ __forceinline__ Span span16(const void* p, uint32_t bytes) {
+    const uintptr_t a = reinterpret_cast<uintptr_t>(p);
+    const uintptr_t lo = a & ~uintptr_t(15);
+    const uintptr_t hi = (a + bytes + 15) & ~uintptr_t(15);
+    Span s;
+    s.src = lo;
+    s.bytes = bytes ? static_cast<uint32_t>(hi - lo) : 0u;
+    return s;
+}
+
+__device__ __forceinline__ int fetch_work(int32_t* head, int lane) {
+    int w = 0;
+    if (lane == 0) w = atomicAdd(head, 1);
+    return __shfl_sync(0xffffffffu, w, 0);
+}
+
+// ------------------------------------------------------------------------------------------
+// Element types.
+template <typename T>
+struct Elem;
+template <>
+struct Elem<float> {
+    static constexpr int VEC = 4;
+};
+template <>
+struct Elem<__nv_bfloat16> {
+    static constexpr int VEC = 8;
+};
+template <>
+struct Elem<__half> {
+    static constexpr int VEC = 8;
+};
+
+__device__ __forceinline__ uint4 ld_gather16(const void* p) { return __ldg(reinterpret_cast<const uint4*>(p)); }
+
+template <typename T>
+__device__ __forceinline__ void unpack(const uint4& r, float* x);
+template <>
+__device__ __forceinline__ void unpack<float>(const uint4& r, float* x) {
+    x[0] = __uint_as_float(r.x);
+    x[1] = __uint_as_float(r.y);
+    x[2] = __uint_as_float(r.z);
+    x[3] = __uint_as_float(r.w);
+}
+template <>
+__device__ __forceinline__ void unpack<__nv_bfloat16>(const uint4& r, float* x) {
+    const uint32_t w[4] = {r.x, r.y, r.z, r.w};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        x[2 * k] = __uint_as_float(w[k] << 16);
+        x[2 * k + 1] = __uint_as_float(w[k] & 0xffff0000u);
+    }
+}
+template <>
+__device__ __forceinline__ void unpack<__half>(const uint4& r, float* x) {
+    const uint32_t w[4] = {r.x, r.y, r.z, r.w};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        __half2 h = *reinterpret_cast<const __half2*>(&w[k]);
+        const float2 f = __half22float2(h);
+        x[2 * k] = f.x;
+        x[2 * k + 1] = f.y;
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ T from_f32(float x);
+template <>
+__device__ __forceinline__ float from_f32<float>(float x) {
+    return x;
+}
+template <>
+__device__ __forceinline__ __nv_bfloat16 from_f32<__nv_bfloat16>(float x) {
+    return __float2bfloat16_rn(x);
+}
+template <>
+__device__ __forceinline__ __half from_f32<__half>(float x) {
+    return __float2half_rn(x);
+}
+
+// N consecutive floats, streaming (read once / written once per step).
+template <int N>
+__device__ __forceinline__ void ld_stream(const float* p, float* x) {
+    if constexpr (N % 4 == 0) {
+#pragma unroll
+        for (int k = 0; k < N / 4; ++k) {
+            const float4 t = __ldcs(reinterpret_cast<const float4*>(p) + k);
+            x[4 * k] = t.x;
+            x[4 * k + 1] = t.y;
+            x[4 * k + 2] = t.z;
+            x[4 * k + 3] = t.w;
+        }
+    } else if constexpr (N == 2) {
+        const float2 t = __ldcs(reinterpret_cast<const float2*>(p));
+        x[0] = t.x;
+        x[1] = t.y;
+    } else {
+        x[0] = __ldcs(p);
+    }
+}
+template <int N>
+__device__ __forceinline__ void st_stream(float* p, const float* x) {
+    if constexpr (N % 4 == 0) {
+#pragma unroll
+        for (int k = 0; k < N / 4; ++k)
+            __stcs(reinterpret_cast<float4*>(p) + k, make_float4(x[4 * k], x[4 * k + 1], x[4 * k + 2], x[4 * k + 3]));
+    } else if constexpr (N == 2) {
+        __stcs(reinterpret_cast<float2*>(p), make_float2(x[0], x[1]));
+    } else {
+        __stcs(p, x[0]);
+    }
+}
+// N consecutive values of T from floats (round to nearest even for 16-bit types).
+template <typename T, int N>
+__device__ __forceinline__ void st_vals(T* p, const float* x) {
+    if constexpr (sizeof(T) == 4) {
+        st_stream<N>(reinterpret_cast<float*>(p), x);
+    } else {
+        uint32_t w[(N + 1) / 2];
+#pragma unroll
+        for (int k = 0; k < (N + 1) / 2; ++k) {
+            const T lo = from_f32<T>(x[2 * k]);
+            const T hi = (2 * k + 1 < N) ? from_f32<T>(x[2 * k + 1]) : from_f32<T>(0.f);
+            w[k] = static_cast<uint32_t>(*reinterpret_cast<const uint16_t*>(&lo)) |
+                   (static_cast<uint32_t>(*reinterpret_cast<const uint16_t*>(&hi)) << 16);
+        }
+        if constexpr (N == 8) {
+            __stcs(reinterpret_cast<uint4*>(p), make_uint4(w[0], w[1], w[2], w[3]));
+        } else if constexpr (N == 4) {
+            __stcs(reinterpret_cast<uint2*>(p), make_uint2(w[0], w[1]));
+        } else if constexpr (N == 2) {
+            __stcs(reinterpret_cast<unsigned int*>(p), w[0]);
+        } else {
+            *p = from_f32<T>(x[0]);
+        }
+    }
+}
+
+__device__ __forceinline__ void kahan_add(float& s, float& c, float x) {
+    const float y = x - c;
+    const float t = s + y;
+    c = (t - s) - y;
+    s = t;
+}
+
+// Logistic sigmoid, overflow-free: with e = exp(-|z|), sigma(|z|) = 1 / (1 + e) and
+// sigma(-|z|) = e / (1 + e).
+__device__ __forceinline__ float sigmoid(float z) {
+    const float e = expf(-fabsf(z));
+    const float r = 1.0f / (1.0f + e);
+    return z >= 0.0f ? r : e * r;
+}
+
+// One Adam step on the logit difference delta given gx = dL/dx, x = sigma(delta / tau); the
+// chain factor sigma(z) sigma(-z) is the product of the two halves above for either sign.
+__device__ __forceinline__ void adam_update(float gx, float& d, float& m, float& v, float& x_new, const AdamK& k) {
+    const float z = d * k.inv_tau;
+    const float e = expf(-fabsf(z));
+    const float r = 1.0f / (1.0f + e);
+    const float q = e * r;
+    const float g = gx * (r * q) * k.inv_tau;
+    m = fmaf(k.beta1, m, k.one_minus_beta1 * g);
+    v = fmaf(k.beta2, v, k.one_minus_beta2 * (g * g));
+    const float den = sqrtf(v) * k.inv_sqrt_bc2 + k.eps;
+    d = d - k.step_size * (m / den);
+    x_new = sigmoid(d * k.inv_tau);
+}
+
+template <int LC, int N>
+__device__ __forceinline__ void group_sum(float (&a)[N]) {
+#pragma unroll
+    for (int off = LC; off < 32; off <<= 1) {
+#pragma unroll
+        for (int e = 0; e < N; ++e) a[e] += __shfl_xor_sync(0xffffffffu, a[e], off);
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+// Variable-major pass: gradient (kModeGrad) or gradient + Adam + relaxed values + rounding
+// (kModeAdam), optionally with the forward loss credited at each clause's position-0 literal.
+
+// Literal factor f = a * x + b on two candidates at once (packed f32x2 arithmetic):
+// (a, b) = (-1, 1) for a positive literal (f = 1 - x), (1, 0) for a negated one (f = x),
+// (0, 1) for the unit-clause sentinel (f = 1, nothing loaded).
+__device__ __forceinline__ float2 dup2(float a) { return make_float2(a, a); }
+
+__device__ __forceinline__ void code_ab(uint32_t c, float& a, float& b) {
+    const bool sent = (c >> kVShift) == kVSentinel;
+    a = sent ? 0.0f : ((c & kVNeg) ? 1.0f : -1.0f);
+    b = sent ? 1.0f : ((c & kVNeg) ? 0.0f : 1.0f);
+}
+
+// General slot loop over the occurrence codes [cs, ce) of the group, NB codes per batch; an
+// occurrence ends at a code carrying kVEnd. R is the running leave-one-out product (prefix then
+// suffix of the occurrence's clause), restarted after each end.
+template <typename T, int VEC, int NB, bool LOSS>
+__device__ __forceinline__ void var_slots(const uint32_t* cd, int cs, int ce, const T* xcol, int64_t ldB, bool ld_ok,
+                                          float (&gacc)[VEC], float (&Ls)[VEC], float (&Lc)[VEC],
+                                          const float (&xs)[VEC]) {
+    constexpr int H = VEC / 2;
+    float2 R[H], G2[H];
+#pragma unroll
+    for (int h = 0; h < H; ++h) {
+        R[h] = dup2(1.0f);
+        G2[h] = make_float2(gacc[2 * h], gacc[2 * h + 1]);
+    }
+    for (int s = cs; s < ce; s += NB) {
+        uint32_t cw[NB];
+        uint4 raw[NB];
+#pragma unroll
+        for (int j = 0; j < NB; ++j) cw[j] = (s + j < ce) ? cd[s + j] : (kVSentinel << kVShift);
+#pragma unroll
+        for (int j = 0; j < NB; ++j) {
+            const uint32_t u = cw[j] >> kVShift;
+            raw[j] = make_uint4(0u, 0u, 0u, 0u);
+            if (ld_ok && u != kVSentinel) raw[j] = ld_gather16(xcol + static_cast<int64_t>(u) * ldB);
+        }
+#pragma unroll
+        for (int j = 0; j < NB; ++j) {
+            float xv[VEC];
+            unpack<T>(raw[j], xv);
+            const uint32_t c = cw[j];
+            float a, b;
+            code_ab(c, a, b);
+            const bool end = (c & kVEnd) != 0u;
+            const float sg = end ? ((c & kVSelfNeg) ? 1.0f : -1.0f) : 0.0f;
+            float2 rn[H];
+#pragma unroll
+            for (int h = 0; h < H; ++h) {
+                rn[h] = __fmul2_rn(R[h], __ffma2_rn(dup2(a), make_float2(xv[2 * h], xv[2 * h + 1]), dup2(b)));
+                G2[h] = __ffma2_rn(dup2(sg), rn[h], G2[h]);
+                R[h] = end ? dup2(1.0f) : rn[h];
+            }
+            if (LOSS && (c & kVCredit)) {
+                const bool sneg = (c & kVSelfNeg) != 0u;
+#pragma unroll
+                for (int h = 0; h < H; ++h) {
+                    kahan_add(Ls[2 * h], Lc[2 * h], (sneg ? xs[2 * h] : 1.0f - xs[2 * h]) * rn[h].x);
+                    kahan_add(Ls[2 * h + 1], Lc[2 * h + 1], (sneg ? xs[2 * h + 1] : 1.0f - xs[2 * h + 1]) * rn[h].y);
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int h = 0; h < H; ++h) {
+        gacc[2 * h] = G2[h].x;
+        gacc[2 * h + 1] = G2[h].y;
+    }
+}
+
+// Fixed-width occurrence loop: every occurrence in [cs, ce) has exactly K codes (all clauses
+// of the tile have width K + 1, e.g. the paper's width-3 normal form with K = 2). OB whole
+// occurrences per batch, their K * OB gathers issued together.
+template <typename T, int VEC, int K, bool LOSS>
+__device__ __forceinline__ void var_occ_fixed(const uint32_t* cd, int cs, int ce, const T* xcol, int64_t ldB,
+                                              bool ld_ok, float (&gacc)[VEC], float (&Ls)[VEC], float (&Lc)[VEC],
+                                              const float (&xs)[VEC]) {
+    constexpr int H = VEC / 2;
+    constexpr int OB = (K == 1) ? 8 : (K == 2 ? 4 : 3);
+    constexpr int NS = OB * K;
+    float2 G2[H];
+#pragma unroll
+    for (int h = 0; h < H; ++h) G2[h] = make_float2(gacc[2 * h], gacc[2 * h + 1]);
+    for (int s = cs; s < ce; s += NS) {
+        uint32_t cw[NS];
+        uint4 raw[NS];
+#pragma unroll
+        for (int j = 0; j < NS; ++j) cw[j] = (s + j < ce) ? cd[s + j] : (kVSentinel << kVShift);
+#pragma unroll
+        for (int j = 0; j < NS; ++j) {
+            const uint32_t u = cw[j] >> kVShift;
+            raw[j] = make_uint4(0u, 0u, 0u, 0u);
+            if (ld_ok && u != kVSentinel) raw[j] = ld_gather16(xcol + static_cast<int64_t>(u) * ldB);
+        }
+#pragma unroll
+        for (int o = 0; o < OB; ++o) {
+            float2 prod[H];
+#pragma unroll
+            for (int j = 0; j < K; ++j) {
+                float xv[VEC];
+                unpack<T>(raw[o * K + j], xv);
+                float a, b;
+                code_ab(cw[o * K + j], a, b);
+#pragma unroll
+                for (int h = 0; h < H; ++h) {
+                    const float2 f = __ffma2_rn(dup2(a), make_float2(xv[2 * h], xv[2 * h + 1]), dup2(b));
+                    prod[h] = (j == 0) ? f : __fmul2_rn(prod[h], f);
+                }
+            }
+            const uint32_t last = cw[o * K + K - 1];
+            const bool valid = (s + o * K) < ce;
+            const float sg = valid ? ((last & kVSelfNeg) ? 1.0f : -1.0f) : 0.0f;
+#pragma unroll
+            for (int h = 0; h < H; ++h) G2[h] = __ffma2_rn(dup2(sg), prod[h], G2[h]);
+            if (LOSS && valid && (last & kVCredit)) {
+                const bool sneg = (last & kVSelfNeg) != 0u;
+#pragma unroll
+                for (int h = 0; h < H; ++h) {
+                    kahan_add(Ls[2 * h], Lc[2 * h], (sneg ? xs[2 * h] : 1.0f - xs[2 * h]) * prod[h].x);
+                    kahan_add(Ls[2 * h + 1], Lc[2 * h + 1], (sneg ? xs[2 * h + 1] : 1.0f - xs[2 * h + 1]) * prod[h].y);
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int h = 0; h < H; ++h) {
+        gacc[2 * h] = G2[h].x;
+        gacc[2 * h + 1] = G2[h].y;
+    }
+}
+
+template <typename T, int VEC, int NB, bool LOSS>
+__device__ __forceinline__ void var_gather(int kk, const uint32_t* cd, int cs, int ce, const T* xcol, int64_t ldB,
+                                           bool ld_ok, float (&gacc)[VEC], float (&Ls)[VEC], float (&Lc)[VEC],
+                                           const float (&xs)[VEC]) {
+    switch (kk) {
+        case 1: var_occ_fixed<T, VEC, 1, LOSS>(cd, cs, ce, xcol, ldB, ld_ok, gacc, Ls, Lc, xs); break;
+        case 2: var_occ_fixed<T, VEC, 2, LOSS>(cd, cs, ce, xcol, ldB, ld_ok, gacc, Ls, Lc, xs); break;
+        case 3: var_occ_fixed<T, VEC, 3, LOSS>(cd, cs, ce, xcol, ldB, ld_ok, gacc, Ls, Lc, xs); break;
+        default: var_slots<T, VEC, NB, LOSS>(cd, cs, ce, xcol, ldB, ld_ok, gacc, Ls, Lc, xs); break;
+    }
+}
+
+template <typename T, int MODE, int LC>
+struct VarCfg {
+    static constexpr int VEC = Elem<T>::VEC;
+    static constexpr int G = 32 / LC;
+    static constexpr int BC = LC * VEC;
+    static constexpr int NB = (VEC == 4) ? 8 : 4;
+    static constexpr int VPG = (VEC / G) > 0 ? (VEC / G) : 1;   // epilogue candidates per lane
+    static constexpr int GE = VEC / VPG;                        // groups active in the epilogue
+    static constexpr int N32 = BC >= 32 ? BC / 32 : 1;          // 32-bit bit-words per chunk
+    static constexpr bool PREFETCH = (VEC == 8);                // Adam state loaded before the gathers
+};
+
+// Adam state (delta, m, v) of the epilogue candidates of one lane.
+template <int VPG>
+struct AdamState {
+    float d[VPG], m[VPG], v[VPG];
+};
+
+template <typename T, int MODE, int LC>
+__device__ __forceinline__ void adam_prefetch(const VarParams& P, int v, int chunk, int g, int li,
+                                              AdamState<VarCfg<T, MODE, LC>::VPG>& st) {
+    using C = VarCfg<T, MODE, LC>;
+    constexpr int VPG = C::VPG;
+    const int c0 = chunk * C::BC + li * C::VEC + g * VPG;
+    const bool act = (g < C::GE) && (c0 < P.B);
+    const int64_t off = static_cast<int64_t>(v) * P.ldB + c0;
+    if (act && c0 + VPG <= P.B) {
+        ld_stream<VPG>(P.delta + off, st.d);
+        ld_stream<VPG>(P.m + off, st.m);
+        ld_stream<VPG>(P.v + off, st.v);
+    } else {
+#pragma unroll
+        for (int el = 0; el < VPG; ++el) {
+            const bool ok = act && c0 + el < P.B;
+            st.d[el] = ok ? P.delta[off + el] : 0.0f;
+            st.m[el] = ok ? P.m[off + el] : 0.0f;
+            st.v[el] = ok ? P.v[off + el] : 0.0f;
+        }
+    }
+}
+
+template <typename T, int MODE, int LC>
+__device__ __forceinline__ void var_epilogue(const VarParams& P, int v, int inst, int chunk, int g, int li, int lane,
+                                             const float (&ge)[VarCfg<T, MODE, LC>::VPG],
+                                             const AdamState<VarCfg<T, MODE, LC>::VPG>& st) {
+    using C = VarCfg<T, MODE, LC>;
+    constexpr int VPG = C::VPG;
+    const int r0 = li * C::VEC + g * VPG;
+    const int c0 = chunk * C::BC + r0;
+    const bool act = (g < C::GE) && (c0 < P.B);
+    const bool full = act && (c0 + VPG <= P.B);
+    const int64_t off = static_cast<int64_t>(v) * P.ldB + c0;
+    if constexpr (MODE == kModeGrad) {
+        if (act) {
+            float out[VPG];
+#pragma unroll
+            for (int el = 0; el < VPG; ++el) {
+                const float s = (P.dloss && c0 + el < P.B)
+                                    ? static_cast<float>(P.dloss[static_cast<int64_t>(inst) * P.B + c0 + el])
+                                    : 1.0f;
+                out[el] = ge[el] * s;
+            }
+            if (full) {
+                st_stream<VPG>(P.grad + off, out);
+            } else {
+                for (int el = 0; el < VPG && c0 + el < P.B; ++el) P.grad[off + el] = out[el];
+            }
+        }
+    } else {
+        uint32_t mybits = 0;
+        if (act) {
+            float d[VPG], mm[VPG], vv[VPG], xn[VPG];
+#pragma unroll
+            for (int el = 0; el < VPG; ++el) {
+                d[el] = st.d[el];
+                mm[el] = st.m[el];
+                vv[el] = st.v[el];
+            }
+#pragma unroll
+            for (int el = 0; el < VPG; ++el) {
+                adam_update(ge[el], d[el], mm[el], vv[el], xn[el], P.adam);
+                if (c0 + el < P.B && d[el] > 0.0f) mybits |= 1u << el;
+            }
+            T* xo = static_cast<T*>(P.x_out) + off;
+            if (full) {
+                st_stream<VPG>(P.delta + off, d);
+                st_stream<VPG>(P.m + off, mm);
+                st_stream<VPG>(P.v + off, vv);
+                st_vals<T, VPG>(xo, xn);
+            } else {
+                for (int el = 0; el < VPG && c0 + el < P.B; ++el) {
+                    P.delta[off + el] = d[el];
+                    P.m[off + el] = mm[el];
+                    P.v[off + el] = vv[el];
+                    xo[el] = from_f32<T>(xn[el]);
+                }
+            }
+        }
+        if (P.bits32) {
+            const int64_t row = static_cast<int64_t>(v) * 2 * P.nwd;
+#pragma unroll
+            for (int wi = 0; wi < C::N32; ++wi) {
+                const uint32_t contrib = (act && (r0 >> 5) == wi) ? (mybits << (r0 & 31)) : 0u;
+                const uint32_t word = __reduce_or_sync(0xffffffffu, contrib);
+                const int hw = chunk * C::N32 + wi;
+                if (lane == 0 && hw < 2 * P.nwd) P.bits32[row + hw] = word;
+            }
+            if (lane == 0 && chunk == P.n_chunks - 1) {
+                for (int hw = P.n_chunks * C::N32; hw < 2 * P.nwd; ++hw) P.bits32[row + hw] = 0u;
+            }
+        }
+    }
+}
+
+template <typename T, int MODE, int LC>
+__device__ __forceinline__ void issue_var_item(const VarParams& P, int item, unsigned char* buf, uint64_t* bar) {
+    using C = VarCfg<T, MODE, LC>;
+    const VarItem it = P.items[item];
+    const Span a = span16(P.vtab + it.vtab_base, static_cast<uint32_t>(it.nv + 1) * 4u);
+    const Span b = (C::G > 1) ? span16(P.recs + it.rec_base, static_cast<uint32_t>(it.n_occ + 1) * 2u) : Span{0, 0};
+    const Span c = span16(P.codes + it.code_base, static_cast<uint32_t>(it.n_codes) * 4u);
+    mbar_expect_tx(bar, a.bytes + b.bytes + c.bytes);
+    if (a.bytes) bulk_g2s(buf, reinterpret_cast<const void*>(a.src), a.bytes, bar);
+    if (b.bytes) bulk_g2s(buf + kVarVtabBytes, reinterpret_cast<const void*>(b.src), b.bytes, bar);
+    if (c.bytes) bulk_g2s(buf + kVarVtabBytes + kVarRecBytes, reinterpret_cast<const void*>(c.src), c.bytes, bar);
+}
+
+template <typename T, int MODE, int LC>
+__device__ __forceinline__ void process_var_item(const VarParams& P, int w, const unsigned char* buf, int g, int li,
+                                                 int lane) {
+    using C = VarCfg<T, MODE, LC>;
+    constexpr int VEC = C::VEC, G = C::G, VPG = C::VPG, GE = C::GE;
+    const int item = w % P.n_items;
+    const int chunk = w / P.n_items;
+    const VarItem it = P.items[item];
+    const uint32_t* vt =
+        reinterpret_cast<const uint32_t*>(buf + (reinterpret_cast<uintptr_t>(P.vtab + it.vtab_base) & 15));
+    const uint16_t* rc = reinterpret_cast<const uint16_t*>(
+        buf + kVarVtabBytes + (reinterpret_cast<uintptr_t>(P.recs + it.rec_base) & 15));
+    const uint32_t* cd = reinterpret_cast<const uint32_t*>(
+        buf + kVarVtabBytes + kVarRecBytes + (reinterpret_cast<uintptr_t>(P.codes + it.code_base) & 15));
+    const int cand0 = chunk * C::BC;
+    const int lane_base = cand0 + li * VEC;
+    const bool ld_ok = lane_base < P.B;
+    const T* xcol = static_cast<const T*>(P.x_in) + lane_base;
+    const bool loss = P.loss_part != nullptr;
+
+    float Ls[VEC], Lc[VEC];
+#pragma unroll
+    for (int e = 0; e < VEC; ++e) Ls[e] = Lc[e] = 0.0f;
+
+    if (it.split < 0) {
+        for (int vi = 0; vi < it.nv; ++vi) {
+            const int v = it.v0 + vi;
+            const uint32_t e0 = vt[vi], e1 = vt[vi + 1];
+            int cs, ce;
+            if constexpr (G == 1) {
+                cs = static_cast<int>(e0 & 0xffffu);
+                ce = static_cast<int>(e1 & 0xffffu);
+            } else {
+                const int oa = static_cast<int>(e0 >> 16);
+                const int O = static_cast<int>(e1 >> 16) - oa;
+                cs = rc[oa + (O * g) / G];
+                ce = rc[oa + (O * (g + 1)) / G];
+            }
+            float xs[VEC];
+#pragma unroll
+            for (int e = 0; e < VEC; ++e) xs[e] = 0.0f;
+            if (loss && ld_ok) unpack<T>(ld_gather16(xcol + static_cast<int64_t>(v) * P.ldB), xs);
+            AdamState<VPG> st;
+            if constexpr (MODE == kModeAdam && C::PREFETCH) adam_prefetch<T, MODE, LC>(P, v, chunk, g, li, st);
+            float gacc[VEC];
+#pragma unroll
+            for (int e = 0; e < VEC; ++e) gacc[e] = 0.0f;
+            if (loss)
+                var_gather<T, VEC, C::NB, true>(it.kk, cd, cs, ce, xcol, P.ldB, ld_ok, gacc, Ls, Lc, xs);
+            else
+                var_gather<T, VEC, C::NB, false>(it.kk, cd, cs, ce, xcol, P.ldB, ld_ok, gacc, Ls, Lc, xs);
+            group_sum<LC>(gacc);
+            float ge[VPG];
+#pragma unroll
+            for (int el = 0; el < VPG; ++el) {
+                float x = gacc[el];
+#pragma unroll
+                for (int q = 1; q < GE; ++q) x = (g == q) ? gacc[q * VPG + el] : x;
+                ge[el] = x;
+            }
+            if constexpr (MODE == kModeAdam && !C::PREFETCH) adam_prefetch<T, MODE, LC>(P, v, chunk, g, li, st);
+            var_epilogue<T, MODE, LC>(P, v, it.inst, chunk, g, li, lane, ge, st);
+        }
+    } else {
+        const int v = it.v0;
+        int cs, ce;
+        if constexpr (G == 1) {
+            cs = 0;
+            ce = it.n_codes;
+        } else {
+            const int O = it.n_occ;
+            cs = rc[(O * g) / G];
+            ce = rc[(O * (g + 1)) / G];
+        }
+        float xs[VEC];
+#pragma unroll
+        for (int e = 0; e < VEC; ++e) xs[e] = 0.0f;
+        if (loss && ld_ok) unpack<T>(ld_gather16(xcol + static_cast<int64_t>(v) * P.ldB), xs);
+        float gacc[VEC];
+#pragma unroll
+        for (int e = 0; e < VEC; ++e) gacc[e] = 0.0f;
+        if (loss)
+            var_gather<T, VEC, C::NB, true>(it.kk, cd, cs, ce, xcol, P.ldB, ld_ok, gacc, Ls, Lc, xs);
+        else
+            var_gather<T, VEC, C::NB, false>(it.kk, cd, cs, ce, xcol, P.ldB, ld_ok, gacc, Ls, Lc, xs);
+        group_sum<LC>(gacc);
+        float* rowp = P.split_part + static_cast<int64_t>(it.split_row + it.part) * P.bpad + lane_base;
+        if (g == 0) {
+#pragma unroll
+            for (int e = 0; e < VEC; e += 4)
+                __stcg(reinterpret_cast<float4*>(rowp + e), make_float4(gacc[e], gacc[e + 1], gacc[e + 2], gacc[e + 3]));
+        }
+        __threadfence();
+        __syncwarp();
+        int prev = 0;
+        if (lane == 0) prev = atomicAdd(&P.split_cnt[static_cast<int64_t>(it.split) * P.n_chunks + chunk], 1);
+        prev = __shfl_sync(0xffffffffu, prev, 0);
+        if (prev == it.n_parts - 1) {
+            __threadfence();
+            float ge[VPG];
+#pragma unroll
+            for (int el = 0; el < VPG; ++el) ge[el] = 0.0f;
+            if (g < GE) {
+                const float* base = P.split_part + static_cast<int64_t>(it.split_row) * P.bpad + lane_base + g * VPG;
+                for (int q = 0; q < it.n_parts; ++q) {
+#pragma unroll
+                    for (int el = 0; el < VPG; ++el) ge[el] += __ldcg(base + static_cast<int64_t>(q) * P.bpad + el);
+                }
+            }
+            AdamState<VPG> st;
+            if constexpr (MODE == kModeAdam) adam_prefetch<T, MODE, LC>(P, v, chunk, g, li, st);
+            var_epilogue<T, MODE, LC>(P, v, it.inst, chunk, g, li, lane, ge, st);
+        }
+    }
+
+    if (loss) {
+        float lf[VEC];
+#pragma unroll
+        for (int e = 0; e < VEC; ++e) lf[e] = Ls[e] - Lc[e];
+        group_sum<LC>(lf);
+        if (g == 0) {
+            float* dst = P.loss_part + static_cast<int64_t>(item) * P.bpad + lane_base;
+#pragma unroll
+            for (int e = 0; e < VEC; e += 4)
+                __stcg(reinterpret_cast<float4*>(dst + e), make_float4(lf[e], lf[e + 1], lf[e + 2], lf[e + 3]));
+        }
+    }
+}
+
+// Register budget: float32 values run 3 CTAs (24 warps) per SM; 16-bit values hold twice the
+// candidates per lane and run 2 CTAs per SM.
+template <typename T, int MODE, int LC>
+__global__ void __launch_bounds__(kThreads, Elem<T>::VEC == 4 ? 3 : 2) k_var_pass(const VarParams P) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int g = lane / LC, li = lane % LC;
+    unsigned char* wbase = smem + warp * kVarWarpBytes;
+    uint64_t* bars = reinterpret_cast<uint64_t*>(wbase + 2 * kVarBufBytes);
+    if (lane == 0) {
+        mbar_init(&bars[0], 1);
+        mbar_init(&bars[1], 1);
+        fence_mbar_init();
+    }
+    __syncwarp();
+    const int total = P.n_items * P.n_chunks;
+    int w = fetch_work(P.head, lane);
+    if (w < total && lane == 0) issue_var_item<T, MODE, LC>(P, w % P.n_items, wbase, &bars[0]);
+    uint32_t phase[2] = {0u, 0u};
+    int buf = 0;
+    while (w < total) {
+        const int wn = fetch_work(P.head, lane);
+        if (wn < total && lane == 0) {
+            fence_proxy_async();
+            issue_var_item<T, MODE, LC>(P, wn % P.n_items, wbase + (buf ^ 1) * kVarBufBytes, &bars[buf ^ 1]);
+        }
+        const bool ok = mbar_wait_bounded(&bars[buf], phase[buf], kWaitNs);
+        if (!__all_sync(0xffffffffu, ok)) {
+            if (lane == 0) {
+                atomicOr(P.status, kStatusTimeout);
+                mbar_wait_bounded(&bars[buf], phase[buf], kWaitNs);
+                if (wn < total) mbar_wait_bounded(&bars[buf ^ 1], phase[buf ^ 1], kWaitNs);
+            }
+            __syncwarp();
+            return;
+        }
+        phase[buf] ^= 1u;
+        process_var_item<T, MODE, LC>(P, w, wbase + buf * kVarBufBytes, g, li, lane);
+        __syncwarp();
+        w = wn;
+        buf ^= 1;
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+// Forward (clause-major): per (clause, candidate) U_t = prod_i f_i, summed per tile.
+template <typename T, int VEC, int NB>
+__device__ __forceinline__ void fwd_slots(const uint32_t* cd, int cs, int ce, const T* xcol, int64_t ldB, bool ld_ok,
+                                          float (&Ls)[VEC], float (&Lc)[VEC]) {
+    constexpr uint32_t kPad = 0xffffffffu;
+    float R[VEC];
+#pragma unroll
+    for (int e = 0; e < VEC; ++e) R[e] = 1.0f;
+    for (int s = cs; s < ce; s += NB) {
+        uint32_t cw[NB];
+        uint4 raw[NB];
+#pragma unroll
+        for (int j = 0; j < NB; ++j) cw[j] = (s + j < ce) ? cd[s + j] : kPad;
+#pragma unroll
+        for (int j = 0; j < NB; ++j) {
+            raw[j] = make_uint4(0u, 0u, 0u, 0u);
+            if (ld_ok && cw[j] != kPad) raw[j] = ld_gather16(xcol + static_cast<int64_t>(cw[j] >> kFShift) * ldB);
+        }
+#pragma unroll
+        for (int j = 0; j < NB; ++j) {
+            float xv[VEC];
+            unpack<T>(raw[j], xv);
+            const uint32_t c = cw[j];
+            const bool pad = (c == kPad);
+            const float a = pad ? 0.0f : ((c & kFNeg) ? 1.0f : -1.0f);
+            const float b = pad ? 1.0f : ((c & kFNeg) ? 0.0f : 1.0f);
+            const bool end = !pad && (c & kFEnd);
+#pragma unroll
+            for (int e = 0; e < VEC; ++e) R[e] *= fmaf(a, xv[e], b);
+            if (end) {
+#pragma unroll
+                for (int e = 0; e < VEC; ++e) {
+                    kahan_add(Ls[e], Lc[e], R[e]);
+                    R[e] = 1.0f;
+                }
+            }
+        }
+    }
+}
+
+__device__ __forceinline__ void issue_fwd_item(const FwdItem* items, const uint32_t* codes, const uint16_t* ctab,
+                                               int item, unsigned char* buf, uint64_t* bar) {
+    const FwdItem it = items[item];
+    const Span a = span16(ctab + it.ctab_base, static_cast<uint32_t>(it.n_clauses + 1) * 2u);
+    const Span c = span16(codes + it.code_base, static_cast<uint32_t>(it.n_codes) * 4u);
+    mbar_expect_tx(bar, a.bytes + c.bytes);
+    if (a.bytes) bulk_g2s(buf, reinterpret_cast<const void*>(a.src), a.bytes, bar);
+    if (c.bytes) bulk_g2s(buf + kFwdCtabBytes, reinterpret_cast<const void*>(c.src), c.bytes, bar);
+}
+
+template <typename T, int LC>
+__global__ void __launch_bounds__(kThreads) k_forward(const FwdParams P) {
+    constexpr int VEC = Elem<T>::VEC, G = 32 / LC, BC = LC * VEC, NB = (VEC == 4) ? 8 : 4;
+    extern __shared__ __align__(128) unsigned char smem[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int g = lane / LC, li = lane % LC;
+    unsigned char* wbase = smem + warp * kFwdWarpBytes;
+    uint64_t* bars = reinterpret_cast<uint64_t*>(wbase + 2 * kFwdBufBytes);
+    if (lane == 0) {
+        mbar_init(&bars[0], 1);
+        mbar_init(&bars[1], 1);
+        fence_mbar_init();
+    }
+    __syncwarp();
+    const int total = P.n_items * P.n_chunks;
+    int w = fetch_work(P.head, lane);
+    if (w < total && lane == 0) issue_fwd_item(P.items, P.codes, P.ctab, w % P.n_items, wbase, &bars[0]);
+    uint32_t phase[2] = {0u, 0u};
+    int buf = 0;
+    while (w < total) {
+        const int wn = fetch_work(P.head, lane);
+        if (wn < total && lane == 0) {
+            fence_proxy_async();
+            issue_fwd_item(P.items, P.codes, P.ctab, wn % P.n_items, wbase + (buf ^ 1) * kFwdBufBytes, &bars[buf ^ 1]);
+        }
+        const bool ok = mbar_wait_bounded(&bars[buf], phase[buf], kWaitNs);
+        if (!__all_sync(0xffffffffu, ok)) {
+            if (lane == 0) {
+                atomicOr(P.status, kStatusTimeout);
+                mbar_wait_bounded(&bars[buf], phase[buf], kWaitNs);
+                if (wn < total) mbar_wait_bounded(&bars[buf ^ 1], phase[buf ^ 1], kWaitNs);
+            }
+            __syncwarp();
+            return;
+        }
+        phase[buf] ^= 1u;
+        {
+            const unsigned char* b = wbase + buf * kFwdBufBytes;
+            const int item = w % P.n_items;
+            const int chunk = w / P.n_items;
+            const FwdItem it = P.items[item];
+            const uint16_t* ct =
+                reinterpret_cast<const uint16_t*>(b + (reinterpret_cast<uintptr_t>(P.ctab + it.ctab_base) & 15));
+            const uint32_t* cd = reinterpret_cast<const uint32_t*>(
+                b + kFwdCtabBytes + (reinterpret_cast<uintptr_t>(P.codes + it.code_base) & 15));
+            const int nc = it.n_clauses;
+            const int cs = ct[(nc * g) / G];
+            const int ce = ct[(nc * (g + 1)) / G];
+            const int lane_base = chunk * BC + li * VEC;
+            const bool ld_ok = lane_base < P.B;
+            const T* xcol = static_cast<const T*>(P.x) + lane_base;
+            float Ls[VEC], Lc[VEC];
+#pragma unroll
+            for (int e = 0; e < VEC; ++e) Ls[e] = Lc[e] = 0.0f;
+            fwd_slots<T, VEC, NB>(cd, cs, ce, xcol, P.ldB, ld_ok, Ls, Lc);
+            float lf[VEC];
+#pragma unroll
+            for (int e = 0; e < VEC; ++e) lf[e] = Ls[e] - Lc[e];
+            group_sum<LC>(lf);
+            if (g == 0) {
+                float* dst = P.loss_part + static_cast<int64_t>(item) * P.bpad + lane_base;
+#pragma unroll
+                for (int e = 0; e < VEC; e += 4)
+                    __stcg(reinterpret_cast<float4*>(dst + e), make_float4(lf[e], lf[e + 1], lf[e + 2], lf[e + 3]));
+            }
+        }
+        __syncwarp();
+        w = wn;
+        buf ^= 1;
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+// Exact check on bit-packed rounded assignments: per clause, sat = OR_i (literal true) over 64
+// candidates per word; unsat words are added into 64 bit-sliced counters per lane. The counters
+// persist across the tiles a warp processes and are flushed (one integer atomic per candidate
+// and lane group) when the instance or word chunk changes, before they could overflow, and at
+// the end of the kernel.
+constexpr int kPlanes = 16;                  // counts < 65536 per lane between flushes
+constexpr int kFlushAt = (1 << kPlanes) - 1 - kFwdClauses;
+
+template <int LW>
+__device__ __forceinline__ void check_flush(uint64_t (&planes)[kPlanes], int32_t* unsat, int inst, int B, int wd,
+                                            int nwd, int g) {
+#pragma unroll
+    for (int off = LW; off < 32; off <<= 1) {
+        uint64_t carry = 0ull;
+#pragma unroll
+        for (int p = 0; p < kPlanes; ++p) {
+            const uint64_t a = planes[p];
+            const uint64_t o = __shfl_xor_sync(0xffffffffu, a, off);
+            const uint64_t s = a ^ o ^ carry;
+            carry = (a & o) | (carry & (a ^ o));
+            planes[p] = s;
+        }
+    }
+    if (g == 0 && wd < nwd) {
+        int32_t* dst = unsat + static_cast<int64_t>(inst) * B + wd * 64;
+        uint64_t any = 0ull;
+#pragma unroll
+        for (int p = 0; p < kPlanes; ++p) any |= planes[p];
+        while (any) {
+            const int bit = __ffsll(static_cast<long long>(any)) - 1;
+            any &= any - 1ull;
+            int cnt = 0;
+#pragma unroll
+            for (int p = 0; p < kPlanes; ++p) cnt |= static_cast<int>((planes[p] >> bit) & 1ull) << p;
+            atomicAdd(dst + bit, cnt);
+        }
+    }
+#pragma unroll
+    for (int p = 0; p < kPlanes; ++p) planes[p] = 0ull;
+}
+
+template <int LW>
+__global__ void __launch_bounds__(kThreads) k_check(const CheckParams P) {
+    constexpr int G = 32 / LW, NB = 8;
+    constexpr uint32_t kPad = 0xffffffffu;
+    extern __shared__ __align__(128) unsigned char smem[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int g = lane / LW, li = lane % LW;
+    unsigned char* wbase = smem + warp * kFwdWarpBytes;
+    uint64_t* bars = reinterpret_cast<uint64_t*>(wbase + 2 * kFwdBufBytes);
+    if (lane == 0) {
+        mbar_init(&bars[0], 1);
+        mbar_init(&bars[1], 1);
+        fence_mbar_init();
+    }
+    __syncwarp();
+    uint64_t planes[kPlanes];
+#pragma unroll
+    for (int p = 0; p < kPlanes; ++p) planes[p] = 0ull;
+    int cur_inst = -1, cur_wd = -1, pending = 0;
+    const int total = P.n_items * P.n_wchunks;
+    int w = fetch_work(P.head, lane);
+    if (w < total && lane == 0) issue_fwd_item(P.items, P.codes, P.ctab, w % P.n_items, wbase, &bars[0]);
+    uint32_t phase[2] = {0u, 0u};
+    int buf = 0;
+    while (w < total) {
+        const int wn = fetch_work(P.head, lane);
+        if (wn < total && lane == 0) {
+            fence_proxy_async();
+            issue_fwd_item(P.items, P.codes, P.ctab, wn % P.n_items, wbase + (buf ^ 1) * kFwdBufBytes, &bars[buf ^ 1]);
+        }
+        const bool ok = mbar_wait_bounded(&bars[buf], phase[buf], kWaitNs);
+        if (!__all_sync(0xffffffffu, ok)) {
+            if (lane == 0) {
+                atomicOr(P.status, kStatusTimeout);
+                mbar_wait_bounded(&bars[buf], phase[buf], kWaitNs);
+                if (wn < total) mbar_wait_bounded(&bars[buf ^ 1], phase[buf ^ 1], kWaitNs);
+            }
+            __syncwarp();
+            return;
+        }
+        phase[buf] ^= 1u;
+        {
+            const unsigned char* b = wbase + buf * kFwdBufBytes;
+            const int item = w % P.n_items;
+            const int wchunk = w / P.n_items;
+            const FwdItem it = P.items[item];
+            const int wd = wchunk * LW + li;
+            if (it.inst != cur_inst || wd != cur_wd || pending > kFlushAt) {
+                if (cur_inst >= 0) check_flush<LW>(planes, P.unsat, cur_inst, P.B, cur_wd, P.nwd, g);
+                cur_inst = it.inst;
+                cur_wd = wd;
+                pending = 0;
+            }
+            pending += it.n_clauses;
+            const uint16_t* ct =
+                reinterpret_cast<const uint16_t*>(b + (reinterpret_cast<uintptr_t>(P.ctab + it.ctab_base) & 15));
+            const uint32_t* cd = reinterpret_cast<const uint32_t*>(
+                b + kFwdCtabBytes + (reinterpret_cast<uintptr_t>(P.codes + it.code_base) & 15));
+            const int nc = it.n_clauses;
+            const int cs = ct[(nc * g) / G];
+            const int ce = ct[(nc * (g + 1)) / G];
+            const bool ok_w = wd < P.nwd;
+            const int rem = P.B - wd * 64;
+            const uint64_t vmask = (!ok_w || rem <= 0) ? 0ull : (rem >= 64 ? ~0ull : ((1ull << rem) - 1ull));
+            uint64_t acc = 0ull;
+            for (int s = cs; s < ce; s += NB) {
+                uint32_t cw[NB];
+                uint64_t x[NB];
+#pragma unroll
+                for (int j = 0; j < NB; ++j) cw[j] = (s + j < ce) ? cd[s + j] : kPad;
+#pragma unroll
+                for (int j = 0; j < NB; ++j)
+                    x[j] = (ok_w && cw[j] != kPad)
+                               ? __ldg(P.bits + static_cast<int64_t>(cw[j] >> kFShift) * P.nwd + wd)
+                               : 0ull;
+#pragma unroll
+                for (int j = 0; j < NB; ++j) {
+                    const uint32_t c = cw[j];
+                    if (c == kPad) continue;
+                    acc |= (c & kFNeg) ? ~x[j] : x[j];
+                    if (c & kFEnd) {
+                        uint64_t carry = ~acc & vmask;
+                        acc = 0ull;
+                        for (int p = 0; p < kPlanes && carry; ++p) {
+                            const uint64_t t = planes[p] & carry;
+                            planes[p] ^= carry;
+                            carry = t;
+                        }
+                    }
+                }
+            }
+        }
+        __syncwarp();
+        w = wn;
+        buf ^= 1;
+    }
+    if (cur_inst >= 0) check_flush<LW>(planes, P.unsat, cur_inst, P.B, cur_wd, P.nwd, g);
+}
+
+// ------------------------------------------------------------------------------------------
+// FP64 reduction of per-tile loss partials, per instance, in tile order.
+__global__ void __launch_bounds__(256) k_loss_reduce(const float* part, int32_t bpad, const int32_t* iptr,
+                                                     const int32_t* items, const int64_t* n_empty, int32_t B,
+                                                     double* loss) {
+    __shared__ double red[8][32];
+    const int inst = blockIdx.y;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int b = blockIdx.x * 32 + lane;
+    const int a = iptr[inst], e = iptr[inst + 1];
+    double s = 0.0;
+    if (b < B)
+        for (int k = a + warp; k < e; k += 8) s += static_cast<double>(part[static_cast<int64_t>(items[k]) * bpad + b]);
+    red[warp][lane] = s;
+    __syncthreads();
+    if (warp == 0 && b < B) {
+        double t = 0.0;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) t += red[q][lane];
+        loss[static_cast<int64_t>(inst) * B + b] = t + static_cast<double>(n_empty[inst]);
+    }
+}
+
+// Adds the always-unsatisfied empty clauses and picks the lowest candidate with the fewest
+// unsatisfied clauses, per instance.
+__global__ void __launch_bounds__(256) k_finalize_check(int32_t* unsat, const int64_t* n_empty, int32_t B,
+                                                        int32_t* best) {
+    __shared__ unsigned long long red[256];
+    const int inst = blockIdx.x;
+    int32_t* u = unsat + static_cast<int64_t>(inst) * B;
+    const int32_t add = static_cast<int32_t>(n_empty[inst]);
+    unsigned long long key = ~0ull;
+    for (int b = threadIdx.x; b < B; b += blockDim.x) {
+        const int32_t c = u[b] + add;
+        u[b] = c;
+        const unsigned long long k = (static_cast<unsigned long long>(static_cast<uint32_t>(c)) << 32) |
+                                     static_cast<uint32_t>(b);
+        key = k < key ? k : key;
+    }
+    red[threadIdx.x] = key;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s && red[threadIdx.x + s] < red[threadIdx.x]) red[threadIdx.x] = red[threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0 && best) best[inst] = (B > 0) ? static_cast<int32_t>(red[0] & 0xffffffffull) : -1;
+}
+
+// Relaxed values x = sigma(delta / tau), written as T.
+template <typename T>
+__global__ void __launch_bounds__(256) k_relax(const float* delta, T* x, int64_t n, int32_t B, int64_t ldB,
+                                               float inv_tau) {
+    const int64_t total = n * B;
+    for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < total;
+         i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const int64_t v = i / B, b = i - v * B;
+        x[v * ldB + b] = from_f32<T>(sigmoid(delta[v * ldB + b] * inv_tau));
+    }
+}
+
+// Rounding (Eq. 4): bit b of row v = (delta[v][b] > 0), 32 candidates per warp ballot.
+__global__ void __launch_bounds__(256) k_round(const float* delta, uint32_t* bits32, int64_t n, int32_t B, int64_t ldB,
+                                               int32_t nwd) {
+    const int lane = threadIdx.x & 31;
+    const int64_t halves = 2LL * nwd;
+    const int64_t total = n * halves;
+    for (int64_t wi = (blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x) >> 5; wi < total;
+         wi += (static_cast<int64_t>(gridDim.x) * blockDim.x) >> 5) {
+        const int64_t v = wi / halves, h = wi - v * halves;
+        const int64_t b = h * 32 + lane;
+        const bool bit = (b < B) && (delta[v * ldB + b] > 0.0f);
+        const uint32_t word = __ballot_sync(0xffffffffu, bit);
+        if (lane == 0) bits32[v * halves + h] = word;
+    }
+}
+
+// Standalone Adam update from an external gradient dL/dx.
+template <typename T>
+__global__ void __launch_bounds__(256) k_adam(float* delta, float* m, float* v, const float* grad, T* x_out, int64_t n,
+                                              int32_t B, int64_t ldB, const AdamK k) {
+    const int64_t total = n * B;
+    for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < total;
+         i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const int64_t r = i / B, b = i - r * B;
+        const int64_t o = r * ldB + b;
+        float d = delta[o], mm = m[o], vv = v[o], xn;
+        adam_update(grad[o], d, mm, vv, xn, k);
+        delta[o] = d;
+        m[o] = mm;
+        v[o] = vv;
+        if (x_out) x_out[o] = from_f32<T>(xn);
+    }
+}
+
+// Self-test of the bounded-wait path: waits on an mbarrier phase that nothing completes (one
+// expected arrival, none made, no copy issued), gives up after limit_ns and records the timeout
+// in the status word. Nothing is in flight when it returns.
+__global__ void k_wait_selftest(int32_t* status, uint64_t limit_ns) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    const bool ok = mbar_wait_bounded(&bar, 0u, limit_ns);
+    if (!__all_sync(0xffffffffu, ok) && threadIdx.x == 0) atomicOr(status, kStatusTimeout);
+}
+
+// ------------------------------------------------------------------------------------------
+int sm_count() {
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (sms <= 0) sms = 1;
+    }
+    return sms;
+}
+
+template <typename K>
+int persistent_grid(K kernel, int smem_bytes) {
+    cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
+    cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kThreads, smem_bytes) != cudaSuccess ||
+        per_sm < 1)
+        per_sm = 1;
+    return per_sm * sm_count();
+}
+
+template <typename T, int MODE, int LC>
+int var_grid_t() {
+    static int grid = 0;
+    if (!grid) grid = persistent_grid(k_var_pass<T, MODE, LC>, kWarps * kVarWarpBytes);
+    return grid;
+}
+template <typename T, int LC>
+int fwd_grid_t() {
+    static int grid = 0;
+    if (!grid) grid = persistent_grid(k_forward<T, LC>, kWarps * kFwdWarpBytes);
+    return grid;
+}
+template <int LW>
+int check_grid_t() {
+    static int grid = 0;
+    if (!grid) grid = persistent_grid(k_check<LW>, kWarps * kFwdWarpBytes);
+    return grid;
+}
+
+template <typename T, int MODE>
+int var_grid_lc(int lc) {
+    switch (lc) {
+        case 32: return var_grid_t<T, MODE, 32>();
+        case 16: return var_grid_t<T, MODE, 16>();
+        case 8: return var_grid_t<T, MODE, 8>();
+        default: return var_grid_t<T, MODE, 4>();
+    }
+}
+template <typename T, int MODE>
+cudaError_t var_launch_lc(const VarParams& p, int lc, int grid, cudaStream_t s) {
+    const int smem = kWarps * kVarWarpBytes;
+    switch (lc) {
+        case 32: var_grid_t<T, MODE, 32>(); k_var_pass<T, MODE, 32><<<grid, kThreads, smem, s>>>(p); break;
+        case 16: var_grid_t<T, MODE, 16>(); k_var_pass<T, MODE, 16><<<grid, kThreads, smem, s>>>(p); break;
+        case 8: var_grid_t<T, MODE, 8>(); k_var_pass<T, MODE, 8><<<grid, kThreads, smem, s>>>(p); break;
+        default: var_grid_t<T, MODE, 4>(); k_var_pass<T, MODE, 4><<<grid, kThreads, smem, s>>>(p); break;
+    }
+    return cudaGetLastError();
+}
+template <typename T>
+cudaError_t fwd_launch_lc(const FwdParams& p, int lc, int grid, cudaStream_t s) {
+    const int smem = kWarps * kFwdWarpBytes;
+    switch (lc) {
+        case 32: fwd_grid_t<T, 32>(); k_forward<T, 32><<<grid, kThreads, smem, s>>>(p); break;
+        case 16: fwd_grid_t<T, 16>(); k_forward<T, 16><<<grid, kThreads, smem, s>>>(p); break;
+        case 8: fwd_grid_t<T, 8>(); k_forward<T, 8><<<grid, kThreads, smem, s>>>(p); break;
+        default: fwd_grid_t<T, 4>(); k_forward<T, 4><<<grid, kThreads, smem, s>>>(p); break;
+    }
+    return cudaGetLastError();
+}
+template <typename T>
+int fwd_grid_lc(int lc) {
+    switch (lc) {
+        case 32: return fwd_grid_t<T, 32>();
+        case 16: return fwd_grid_t<T, 16>();
+        case 8: return fwd_grid_t<T, 8>();
+        default: return fwd_grid_t<T, 4>();
+    }
+}
+
+int elementwise_grid(int64_t total) {
+    const int64_t blocks = (total + 255) / 256;
+    const int64_t cap = static_cast<int64_t>(sm_count()) * 8;
+    return static_cast<int>(blocks < 1 ? 1 : (blocks < cap ? blocks : cap));
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------------------------------
+int grid_var_pass(int dtype, int mode, int lc) {
+    if (dtype == kF32) return mode == kModeAdam ? var_grid_lc<float, kModeAdam>(lc) : var_grid_lc<float, kModeGrad>(lc);
+    if (dtype == kBF16)
+        return mode == kModeAdam ? var_grid_lc<__nv_bfloat16, kModeAdam>(lc) : var_grid_lc<__nv_bfloat16, kModeGrad>(lc);
+    return mode == kModeAdam ? var_grid_lc<__half, kModeAdam>(lc) : var_grid_lc<__half, kModeGrad>(lc);
+}
+int grid_forward(int dtype, int lc) {
+    if (dtype == kF32) return fwd_grid_lc<float>(lc);
+    if (dtype == kBF16) return fwd_grid_lc<__nv_bfloat16>(lc);
+    return fwd_grid_lc<__half>(lc);
+}
+int grid_check(int lw) {
+    switch (lw) {
+        case 32: return check_grid_t<32>();
+        case 16: return check_grid_t<16>();
+        case 8: return check_grid_t<8>();
+        case 4: return check_grid_t<4>();
+        case 2: return check_grid_t<2>();
+        default: return check_grid_t<1>();
+    }
+}
+
+cudaError_t launch_var_pass(const VarParams& p, int dtype, int mode, int lc, int grid, cudaStream_t s) {
+    if (dtype == kF32)
+        return mode == kModeAdam ? var_launch_lc<float, kModeAdam>(p, lc, grid, s)
+                                 : var_launch_lc<float, kModeGrad>(p, lc, grid, s);
+    if (dtype == kBF16)
+        return mode == kModeAdam ? var_launch_lc<__nv_bfloat16, kModeAdam>(p, lc, grid, s)
+                                 : var_launch_lc<__nv_bfloat16, kModeGrad>(p, lc, grid, s);
+    return mode == kModeAdam ? var_launch_lc<__half, kModeAdam>(p, lc, grid, s)
+                             : var_launch_lc<__half, kModeGrad>(p, lc, grid, s);
+}
+
+cudaError_t launch_forward(const FwdParams& p, int dtype, int lc, int grid, cudaStream_t s) {
+    if (dtype == kF32) return fwd_launch_lc<float>(p, lc, grid, s);
+    if (dtype == kBF16) return fwd_launch_lc<__nv_bfloat16>(p, lc, grid, s);
+    return fwd_launch_lc<__half>(p, lc, grid, s);
+}
+
+cudaError_t launch_check(const CheckParams& p, int lw, int grid, cudaStream_t s) {
+    const int smem = kWarps * kFwdWarpBytes;
+    switch (lw) {
+        case 32: check_grid_t<32>(); k_check<32><<<grid, kThreads, smem, s>>>(p); break;
+        case 16: check_grid_t<16>(); k_check<16><<<grid, kThreads, smem, s>>>(p); break;
+        case 8: check_grid_t<8>(); k_check<8><<<grid, kThreads, smem, s>>>(p); break;
+        case 4: check_grid_t<4>(); k_check<4><<<grid, kThreads, smem, s>>>(p); break;
+        case 2: check_grid_t<2>(); k_check<2><<<grid, kThreads, smem, s>>>(p); break;
+        default: check_grid_t<1>(); k_check<1><<<grid, kThreads, smem, s>>>(p); break;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_loss_reduce(const float* part, int32_t bpad, const int32_t* inst_items_ptr,
+                               const int32_t* inst_items, const int64_t* n_empty, int32_t n_inst, int32_t B,
+                               double* loss, cudaStream_t s) {
+    if (B <= 0 || n_inst <= 0) return cudaSuccess;
+    dim3 grid((B + 31) / 32, n_inst);
+    k_loss_reduce<<<grid, 256, 0, s>>>(part, bpad, inst_items_ptr, inst_items, n_empty, B, loss);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_finalize_check(int32_t* unsat, const int64_t* n_empty, int32_t n_inst, int32_t B, int32_t* best,
+                                  cudaStream_t s) {
+    if (n_inst <= 0) return cudaSuccess;
+    k_finalize_check<<<n_inst, 256, 0, s>>>(unsat, n_empty, B, best);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_relax(const float* delta, void* x, int dtype, int64_t n, int32_t B, int64_t ldB, float inv_tau,
+                         cudaStream_t s) {
+    if (n * B == 0) return cudaSuccess;
+    const int grid = elementwise_grid(n * B);
+    if (dtype == kF32)
+        k_relax<float><<<grid, 256, 0, s>>>(delta, static_cast<float*>(x), n, B, ldB, inv_tau);
+    else if (dtype == kBF16)
+        k_relax<__nv_bfloat16><<<grid, 256, 0, s>>>(delta, static_cast<__nv_bfloat16*>(x), n, B, ldB, inv_tau);
+    else
+        k_relax<__half><<<grid, 256, 0, s>>>(delta, static_cast<__half*>(x), n, B, ldB, inv_tau);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_round(const float* delta, uint32_t* bits32, int64_t n, int32_t B, int64_t ldB, int32_t nwd,
+                         cudaStream_t s) {
+    const int64_t warps = n * 2 * nwd;
+    if (warps == 0) return cudaSuccess;
+    k_round<<<elementwise_grid(warps * 32), 256, 0, s>>>(delta, bits32, n, B, ldB, nwd);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adam(float* delta, float* m, float* v, const float* grad, void* x_out, int dtype, int64_t n,
+                        int32_t B, int64_t ldB, const AdamK& k, cudaStream_t s) {
+    if (n * B == 0) return cudaSuccess;
+    const int grid = elementwise_grid(n * B);
+    if (dtype == kF32)
+        k_adam<float><<<grid, 256, 0, s>>>(delta, m, v, grad, static_cast<float*>(x_out), n, B, ldB, k);
+    else if (dtype == kBF16)
+        k_adam<__nv_bfloat16><<<grid, 256, 0, s>>>(delta, m, v, grad, static_cast<__nv_bfloat16*>(x_out), n, B, ldB, k);
+    else
+        k_adam<__half><<<grid, 256, 0, s>>>(delta, m, v, grad, static_cast<__half*>(x_out), n, B, ldB, k);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_wait_selftest(int32_t* status, uint64_t limit_ns, cudaStream_t s) {
+    k_wait_selftest<<<1, 32, 0, s>>>(status, limit_ns);
+    return cudaGetLastError();
+}
+
+}  // namespace gs

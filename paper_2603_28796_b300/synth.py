@@ -157,7 +157,8 @@ def concat(parts: List[CNF], name: str = "") -> Batch:
         off_c += p.n_clauses
         off_l += p.nnz
     lits = np.concatenate([p.lits for p in parts]) if parts else np.zeros(0, np.int32)
-    xs = np.concatenate([p.xstar for p in parts]) if parts else np.zeros(0, np.uint8)
+    xs = np.concatenate([p.xstar if p.xstar is not None else np.zeros(p.n_vars, np.uint8) for p in parts]) \
+        if parts else np.zeros(0, np.uint8)
     return Batch(nv, nc, cp, lits.astype(np.int32), xs, name)
 
 

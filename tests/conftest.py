@@ -10,14 +10,16 @@ if ROOT not in sys.path:
 
 def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA GPU (runs the sm_103a kernels)")
+    config.addinivalue_line("markers", "slow: longer test")
 
 
 @pytest.fixture(scope="session", autouse=True)
 def _native_builds():
-    """Compile the oracle and the input generators if they are stale."""
+    """Compile the oracle, the input generators and the C-ABI library if they are stale."""
     import oracle
     from paper_2603_28796_b300 import build
 
     oracle.build()
     build.build_synth()
+    build.build_library()
     yield

@@ -1,0 +1,175 @@
+"""Full-size GPU checks at the workloads' sizes and in the benchmark's launch configuration.
+
+The oracle is exact per candidate column and candidates are independent, so it is run on a
+sample of columns of the same seeded inputs (oracle(x[:, S]) == oracle(x)[:, S]); everything
+else is checked through properties that hold at any size.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle  # noqa: E402
+from paper_2603_28796_b300 import _abi, synth  # noqa: E402
+from paper_2603_28796_b300.engine import Engine, GSLoss, candidates  # noqa: E402
+from tests import _gpu_helpers as H  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+_cache = {}
+
+
+def workload(name):
+    if name not in _cache:
+        cnf = synth.workload_cnf(name, seed=0)
+        _cache[name] = (cnf, H.load(cnf))
+    return _cache[name]
+
+
+SAMPLE = np.array([0, 1, 127, 128, 500, 777, 1022, 1023])
+
+
+def test_differentiation_fused_step_sampled_parity():
+    cnf, prob = workload("differentiation")
+    n, B, t = cnf.n_vars, 1024, 2
+    d0 = synth.init_delta(n, B, seed=101)
+    m0 = synth.normal_values(n, B, seed=102, scale=0.02)
+    v0 = np.abs(synth.normal_values(n, B, seed=103, scale=0.005))
+    x0 = synth.uniform_values(n, B, seed=104)
+    delta, m, v, xin = (H.device_cands(a, B) for a in (d0, m0, v0, x0))
+    xout = candidates(n, B)
+    bits = torch.zeros((n, B // 64), dtype=torch.int64, device="cuda")
+    loss = torch.zeros((1, B), dtype=torch.float64, device="cuda")
+    _abi.gs_step(prob, delta, m, v, t, x_in=xin, x_out=xout, loss=loss, bits=bits)
+    grad = _abi.gs_backward(prob, xin)
+    fl = _abi.gs_forward(prob, xin)
+    torch.cuda.synchronize()
+    S = SAMPLE
+    xs = x0[:, S].astype(np.float64)
+    lu, _ = oracle.forward(n, cnf.clause_ptr, cnf.lits, xs)
+    g_ref, scale = oracle.backward(n, cnf.clause_ptr, cnf.lits, xs)
+    d_ref, m_ref, v_ref, _ = oracle.adam(d0[:, S], m0[:, S], v0[:, S], g_ref, t)
+    H.assert_loss(loss.cpu().numpy()[0][S], lu, "fused loss")
+    H.assert_loss(fl.cpu().numpy()[0][S], lu, "forward loss")
+    H.assert_grad(H.host64(grad)[:, S], g_ref, scale)
+    tol = H.adam_tolerances(d0[:, S], m0[:, S], v0[:, S], g_ref, scale, t)
+    out = dict(delta=H.host64(delta)[:, S], m=H.host64(m)[:, S], v=H.host64(v)[:, S])
+    H.check_adam(out, dict(delta=d_ref, m=m_ref, v=v_ref), tol, "differentiation workload")
+    dg = H.host64(delta)
+    assert np.array_equal(H.unpack_bits(bits, n, B), (dg > 0).astype(np.uint8))   # all columns
+
+
+def test_differentiation_round_check_sampled():
+    cnf, prob = workload("differentiation")
+    n, B = cnf.n_vars, 1024
+    d = synth.normal_values(n, B, seed=105)
+    d[::13, ::7] = 0.0
+    unsat, best = _abi.gs_round_check(prob, H.device_cands(d, B))
+    torch.cuda.synchronize()
+    _, u_ref, _ = oracle.round_check(n, cnf.clause_ptr, cnf.lits, d[:, SAMPLE].astype(np.float64))
+    u = unsat.cpu().numpy()[0]
+    assert np.array_equal(u[SAMPLE], u_ref)
+    b = int(best.cpu()[0])
+    assert u[b] == u.min() and np.all(u[:b] > u.min())
+
+
+def test_differentiation_autograd_matches_finite_differences():
+    """P7 on the GPU: the loss is affine in each coordinate for distinct-variable clauses, so the
+    central difference with h = 0.25 equals the gradient up to the float32 loss error. 256
+    coordinates, each in its own candidate column, are perturbed in one pair of forward passes."""
+    cnf, prob = workload("differentiation")
+    n, B = cnf.n_vars, 1024
+    rng = np.random.default_rng(106)
+    x0 = synth.uniform_values(n, B, seed=107)
+    x = H.device_cands(x0, B).requires_grad_(True)
+    loss = GSLoss.apply(x, prob)
+    w = torch.from_numpy(rng.uniform(0.5, 1.5, size=(1, B))).cuda()
+    (loss * w).sum().backward()
+    g = H.host64(x.grad)
+    cols = rng.choice(B, size=256, replace=False)
+    rows = rng.integers(0, n, size=256)
+    h = 0.25
+    xp, xm = x0.copy(), x0.copy()
+    xp[rows, cols] += h
+    xm[rows, cols] -= h
+    lp = _abi.gs_forward(prob, H.device_cands(xp, B)).cpu().numpy()[0]
+    lm = _abi.gs_forward(prob, H.device_cands(xm, B)).cpu().numpy()[0]
+    l0 = loss.detach().cpu().numpy()[0]
+    wc = w.cpu().numpy()[0][cols]
+    fd = (lp[cols] - lm[cols]) / (2 * h) * wc
+    # loss error bound: every clause product is within a few ulp and tile sums are
+    # compensated, so each evaluation is within 1e-6 * L of exact
+    err_l = 1e-6 * (np.abs(lp[cols]) + np.abs(lm[cols]))
+    xs = x0[:, cols].astype(np.float64)
+    g_ref, scale = oracle.backward(n, cnf.clause_ptr, cnf.lits, xs)
+    gsel = g[rows, cols]
+    ref_sel = g_ref[rows, np.arange(256)] * wc
+    sc = scale[rows, np.arange(256)] * wc
+    assert np.all(np.abs(fd - gsel) <= 1e-5 * np.maximum(np.abs(gsel), sc) + err_l * wc / (2 * h) * 1.5)
+    assert np.all(np.abs(gsel - ref_sel) <= 1e-5 * np.maximum(np.abs(ref_sel), sc))
+    assert np.all(l0 > 0)
+
+
+def test_plain_workload_1000_steps():
+    """Plain method: planted 3-SAT n=200, m=852, B=64, 1000 graph-captured steps. The unsat
+    counts of the final rounded assignments are re-checked on the host by direct Boolean
+    evaluation, the loss decreases, and the first steps track the FP64 oracle's trajectory."""
+    cnf, prob = workload("plain")
+    n, B = cnf.n_vars, 64
+    eng = Engine(prob, B, "f32", seed=7)
+    first = []
+    for _ in range(5):
+        eng.step()
+        first.append(eng.delta.detach().cpu().numpy().astype(np.float64).copy())
+    l5 = eng.loss.cpu().numpy()[0].copy()
+    eng.run(994, graph=True)
+    eng.step()
+    torch.cuda.synchronize()
+    unsat, best = eng.round_check()
+    torch.cuda.synchronize()
+    u = unsat.cpu().numpy()[0]
+    # host re-check of the rounded assignments (Boolean evaluation, independent of the kernels)
+    xh = H.unpack_bits(eng.bits, n, B)
+    lits = cnf.lits.astype(np.int64)
+    vv = np.abs(lits) - 1
+    for b in range(B):
+        true = np.where(lits > 0, xh[vv, b] == 1, xh[vv, b] == 0)
+        sat = np.logical_or.reduceat(true, cnf.clause_ptr[:-1])
+        assert int((~sat).sum()) == u[b]
+    lf = eng.loss.cpu().numpy()[0]
+    assert np.median(lf) < 0.5 * np.median(l5)
+    # trajectory: oracle from the same seeded initialisation, first 5 steps
+    d = synth.init_delta(n, B, seed=7).astype(np.float64)
+    mm, vv2 = np.zeros_like(d), np.zeros_like(d)
+    x = oracle.relax(d)
+    for t in range(1, 6):
+        g, _ = oracle.backward(n, cnf.clause_ptr, cnf.lits, x)
+        d, mm, vv2, x = oracle.adam(d, mm, vv2, g, t)
+        close = np.abs(first[t - 1] - d) <= 1e-3 * (1 + np.abs(d))
+        assert close.mean() > 0.99, (t, close.mean())
+
+
+@pytest.mark.parametrize("dtype", ["bf16", "f32"])
+def test_precision_workload_sampled_parity(dtype):
+    """Mixed widths 2..12, power-law occurrences (hub variables split over many tiles),
+    n = 2,000,000, m = 8,000,000, B = 256."""
+    cnf, prob = workload("precision")
+    n, B, t = cnf.n_vars, 256, 1
+    S = np.array([0, 5, 100, 255])
+    x0 = synth.uniform_values(n, B, seed=201)
+    xin = H.device_cands(x0, B, dtype)
+    d0 = synth.init_delta(n, B, seed=202)
+    z = np.zeros((n, B), np.float32)
+    delta, m, v = (H.device_cands(a, B) for a in (d0, z, z))
+    xout = candidates(n, B, H.TORCH_DT[dtype])
+    loss = torch.zeros((1, B), dtype=torch.float64, device="cuda")
+    _abi.gs_step(prob, delta, m, v, t, x_in=xin, x_out=xout, loss=loss)
+    torch.cuda.synchronize()
+    xs = H.host64(xin)[:, S]
+    lu, _ = oracle.forward(n, cnf.clause_ptr, cnf.lits, xs)
+    g_ref, scale = oracle.backward(n, cnf.clause_ptr, cnf.lits, xs)
+    d_ref, m_ref, v_ref, _ = oracle.adam(d0[:, S], z[:, S], z[:, S], g_ref, t)
+    H.assert_loss(loss.cpu().numpy()[0][S], lu, "precision loss")
+    tol = H.adam_tolerances(d0[:, S], z[:, S], z[:, S], g_ref, scale, t)
+    out = dict(delta=H.host64(delta)[:, S], m=H.host64(m)[:, S], v=H.host64(v)[:, S])
+    H.check_adam(out, dict(delta=d_ref, m=m_ref, v=v_ref), tol, "precision workload %s" % dtype)

@@ -1,0 +1,306 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle, element by element.
+
+Every input comes from the seeded generators; the oracle sees the same values in float64
+(16-bit inputs are generated already rounded to their dtype). Bars: rounded assignments, unsat
+counts and best candidates bit-exact; loss within 1e-5 relative; gradient within
+1e-5 * max(|g|, A) with A = sum |leave-one-out|; Adam outputs within the bound propagated from
+those through float32 arithmetic (tests/_gpu_helpers.adam_tolerances).
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle  # noqa: E402
+from paper_2603_28796_b300 import _abi, synth  # noqa: E402
+from paper_2603_28796_b300.engine import Engine, candidates  # noqa: E402
+from tests import _gpu_helpers as H  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+def edge_cnf():
+    """Empty, unit, duplicate-literal and tautological clauses, a variable with no occurrence,
+    and a hub variable whose occurrence list is split over several tiles."""
+    rng = np.random.default_rng(9)
+    n = 40
+    clauses = [[], [3], [-7], [5, 5, -2], [4, -4, 9], [], [1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12]]
+    for _ in range(300):                       # hub: variable 20 in 300 clauses (> one tile)
+        others = rng.choice([v for v in range(1, n + 1) if v not in (20, 40)], size=2, replace=False)
+        s = rng.integers(0, 2, size=3)
+        clauses.append([20 if s[0] else -20] + [int(o) if si else -int(o) for o, si in zip(others, s[1:])])
+    for _ in range(60):
+        k = int(rng.integers(1, 6))
+        vs = rng.choice(np.arange(1, 40), size=k, replace=False)
+        clauses.append([int(v) if rng.integers(0, 2) else -int(v) for v in vs])
+    cp = np.zeros(len(clauses) + 1, dtype=np.int64)
+    for t, c in enumerate(clauses):
+        cp[t + 1] = cp[t] + len(c)
+    lits = np.array([l for c in clauses for l in c], dtype=np.int32)
+    return synth.CNF(n, cp, lits, None, "edge cases")   # variable 40 never occurs
+
+
+CNFS = {
+    "3sat": lambda: synth.planted_ksat(1500, 6390, 3, seed=21),
+    "mixed": lambda: synth.mixed_powerlaw(3000, 10000, seed=22),      # power-law hubs -> split tiles
+    "community": lambda: synth.community(8 * 400, 4 * 8 * 400, 8, seed=23),
+    "edge": edge_cnf,
+}
+_cache = {}
+
+
+def get(name):
+    if name not in _cache:
+        cnf = CNFS[name]()
+        _cache[name] = (cnf, H.load(cnf))
+    return _cache[name]
+
+
+# ---------------------------------------------------------------------------------------------
+@pytest.mark.parametrize("dtype", ["f32", "bf16", "f16"])
+@pytest.mark.parametrize("B", [1, 7, 64, 100, 300])
+@pytest.mark.parametrize("name", ["3sat", "mixed", "edge"])
+def test_forward_and_backward(name, B, dtype):
+    cnf, prob = get(name)
+    x = H.device_cands(synth.uniform_values(cnf.n_vars, B, seed=B), B, dtype)
+    xh = H.host64(x)
+    loss = _abi.gs_forward(prob, x)
+    grad = _abi.gs_backward(prob, x)
+    torch.cuda.synchronize()
+    lu, _ = oracle.forward(cnf.n_vars, cnf.clause_ptr, cnf.lits, xh)
+    g_ref, scale = oracle.backward(cnf.n_vars, cnf.clause_ptr, cnf.lits, xh)
+    H.assert_loss(loss.cpu().numpy()[0], lu)
+    H.assert_grad(H.host64(grad), g_ref, scale)
+
+
+@pytest.mark.parametrize("B", [33, 1024 + 40])
+def test_forward_backward_many_chunks(B):
+    cnf, prob = get("3sat")
+    x = H.device_cands(synth.uniform_values(cnf.n_vars, B, seed=3), B, "f32")
+    xh = H.host64(x)
+    dl = torch.from_numpy(synth.normal_values(1, B, seed=4)[0].astype(np.float64)).cuda().reshape(1, B)
+    loss = _abi.gs_forward(prob, x)
+    grad = _abi.gs_backward(prob, x, dloss=dl)
+    torch.cuda.synchronize()
+    lu, _ = oracle.forward(cnf.n_vars, cnf.clause_ptr, cnf.lits, xh)
+    g_ref, scale = oracle.backward(cnf.n_vars, cnf.clause_ptr, cnf.lits, xh)
+    w = dl.cpu().numpy()[0].astype(np.float32).astype(np.float64)
+    H.assert_loss(loss.cpu().numpy()[0], lu)
+    H.assert_grad(H.host64(grad), g_ref * w, scale * np.abs(w))
+
+
+def test_boolean_points_exact():
+    # At Boolean x the loss is the unsat count and the gradient an integer (exact at zeros).
+    cnf, prob = get("mixed")
+    B = 96
+    xb = (synth.uniform_values(cnf.n_vars, B, seed=5) > 0.5).astype(np.float32)
+    x = H.device_cands(xb, B)
+    loss = _abi.gs_forward(prob, x)
+    grad = _abi.gs_backward(prob, x)
+    torch.cuda.synchronize()
+    lu, _ = oracle.forward(cnf.n_vars, cnf.clause_ptr, cnf.lits, xb.astype(np.float64))
+    g_ref, _ = oracle.backward(cnf.n_vars, cnf.clause_ptr, cnf.lits, xb.astype(np.float64))
+    assert np.array_equal(loss.cpu().numpy()[0], lu)
+    assert np.array_equal(H.host64(grad), g_ref)
+    unsat, best = _abi.gs_round_check(prob, H.device_cands(2 * xb - 1, B))
+    assert np.array_equal(unsat.cpu().numpy()[0], lu.astype(np.int32))
+
+
+@pytest.mark.parametrize("dtype", ["f32", "bf16"])
+@pytest.mark.parametrize("B", [5, 64, 200])
+@pytest.mark.parametrize("name", ["3sat", "mixed", "edge", "community"])
+def test_fused_step(name, B, dtype):
+    cnf, prob = get(name)
+    n = cnf.n_vars
+    t = 3
+    d0 = synth.init_delta(n, B, seed=11)
+    m0 = synth.normal_values(n, B, seed=12, scale=0.05)
+    v0 = np.abs(synth.normal_values(n, B, seed=13, scale=0.01))
+    xin = H.device_cands(synth.uniform_values(n, B, seed=14), B, dtype)
+    delta, m, v = (H.device_cands(a, B) for a in (d0, m0, v0))
+    xout = candidates(n, B, H.TORCH_DT[dtype], fill=-1.0)
+    bits = torch.zeros((n, (B + 63) // 64), dtype=torch.int64, device="cuda")
+    loss = torch.zeros((1, B), dtype=torch.float64, device="cuda")
+    _abi.gs_step(prob, delta, m, v, t, x_in=xin, x_out=xout, loss=loss, bits=bits)
+    torch.cuda.synchronize()
+    xh = H.host64(xin)
+    lu, _ = oracle.forward(n, cnf.clause_ptr, cnf.lits, xh)
+    g_ref, scale = oracle.backward(n, cnf.clause_ptr, cnf.lits, xh)
+    d_ref, m_ref, v_ref, x_ref = oracle.adam(d0[:, :B], m0[:, :B], v0[:, :B], g_ref, t)
+    H.assert_loss(loss.cpu().numpy()[0], lu, "fused loss")
+    tol = H.adam_tolerances(d0[:, :B], m0[:, :B], v0[:, :B], g_ref, scale, t)
+    out = dict(delta=H.host64(delta), m=H.host64(m), v=H.host64(v))
+    H.check_adam(out, dict(delta=d_ref, m=m_ref, v=v_ref), tol, "fused %s B=%d %s" % (name, B, dtype))
+    # x_out = sigma(delta') rounded to dtype; bits = [delta' > 0] (properties of the outputs)
+    dg = out["delta"]
+    sig = 1.0 / (1.0 + np.exp(-dg))
+    xo = H.host64(xout)
+    rel = {"f32": 10 * H.U32, "bf16": 2.0 ** -8, "f16": 2.0 ** -11}[dtype]
+    assert np.all(np.abs(xo - sig) <= rel * sig + 1e-38 + (2.0 ** -24 if dtype == "f16" else 0.0))
+    assert np.array_equal(H.unpack_bits(bits, n, B), (dg > 0).astype(np.uint8))
+    assert H.padding_bits_zero(bits, n, B)
+    # where the oracle's delta' is clear of zero by more than the bound, the rounding agrees
+    clear = np.abs(d_ref) > tol["delta"]
+    assert np.array_equal(((dg > 0) == (d_ref > 0))[clear], np.ones(clear.sum(), bool))
+
+
+@pytest.mark.parametrize("dtype", ["f32", "f16"])
+def test_step_with_external_gradient(dtype):
+    cnf, prob = get("3sat")
+    n, B, t = cnf.n_vars, 96, 1
+    d0 = synth.init_delta(n, B, seed=31)
+    g = synth.normal_values(n, B, seed=32, scale=2.0)
+    z = np.zeros((n, B), np.float32)
+    delta, m, v, grad = (H.device_cands(a, B) for a in (d0, z, z, g))
+    xout = candidates(n, B, H.TORCH_DT[dtype])
+    _abi.gs_step(prob, delta, m, v, t, grad=grad, x_out=xout)
+    torch.cuda.synchronize()
+    d_ref, m_ref, v_ref, _ = oracle.adam(d0, z, z, g, t)
+    tol = H.adam_tolerances(d0, z, z, g, None, t, g_rel=0.0)
+    H.check_adam(dict(delta=H.host64(delta), m=H.host64(m), v=H.host64(v)), dict(delta=d_ref, m=m_ref, v=v_ref), tol)
+
+
+@pytest.mark.parametrize("B", [1, 63, 64, 65, 130, 1000])
+@pytest.mark.parametrize("name", ["3sat", "mixed", "edge", "community"])
+def test_round_check_bit_exact(name, B):
+    cnf, prob = get(name)
+    n = cnf.n_vars
+    d = synth.normal_values(n, B, seed=41 + B)
+    d[::7, ::3] = 0.0                        # ties go to state 0
+    d[1::11, ::5] = -0.0
+    delta = H.device_cands(d, B)
+    bits = torch.zeros((n, (B + 63) // 64), dtype=torch.int64, device="cuda")
+    unsat, best = _abi.gs_round_check(prob, delta, bits=bits)
+    torch.cuda.synchronize()
+    xh, u_ref, b_ref = oracle.round_check(n, cnf.clause_ptr, cnf.lits, d.astype(np.float64))
+    assert np.array_equal(H.unpack_bits(bits, n, B), xh)
+    assert H.padding_bits_zero(bits, n, B)
+    assert np.array_equal(unsat.cpu().numpy()[0], u_ref)
+    assert int(best.cpu().numpy()[0]) == b_ref
+    # the same through the bits-only entry point
+    u2, b2 = _abi.gs_check_bits(prob, bits, B)
+    assert np.array_equal(u2.cpu().numpy()[0], u_ref) and int(b2[0]) == b_ref
+
+
+def test_planted_assignment_has_no_unsat_clause():
+    cnf, prob = get("community")
+    B = 70
+    d = np.repeat((2.0 * cnf.xstar.astype(np.float32) - 1.0)[:, None], B, axis=1)
+    d[:, 1::2] = -d[:, 1::2]                 # odd candidates: the complement
+    unsat, best = _abi.gs_round_check(prob, H.device_cands(d, B))
+    u = unsat.cpu().numpy()[0]
+    assert np.all(u[0::2] == 0) and int(best[0]) == 0
+    _, u_ref, _ = oracle.round_check(cnf.n_vars, cnf.clause_ptr, cnf.lits, d.astype(np.float64))
+    assert np.array_equal(u, u_ref)
+
+
+@pytest.mark.parametrize("dtype", ["f32", "bf16", "f16"])
+def test_relax(dtype):
+    cnf, prob = get("3sat")
+    n, B = cnf.n_vars, 40
+    d = synth.normal_values(n, B, seed=51, scale=6.0)
+    delta = H.device_cands(d, B)
+    x = candidates(n, B, H.TORCH_DT[dtype])
+    _abi.gs_relax(prob, delta, x, tau=1.0)
+    torch.cuda.synchronize()
+    ref = oracle.relax(d.astype(np.float64))
+    rel = {"f32": 10 * H.U32, "bf16": 2.0 ** -8, "f16": 2.0 ** -11}[dtype]
+    assert np.all(np.abs(H.host64(x) - ref) <= rel * ref + (2.0 ** -24 if dtype == "f16" else 1e-38))
+
+
+def test_batch_instances():
+    parts = [synth.planted_ksat(300 + 50 * i, int(4.2 * (300 + 50 * i)), 3 + (i % 2), seed=60 + i) for i in range(5)]
+    parts.append(edge_cnf())
+    batch = synth.concat(parts)
+    prob = _abi.gs_load_batch(batch.n_vars, batch.n_clauses, batch.clause_ptr, batch.lits)
+    assert prob.n_inst == 6
+    n, B = int(batch.n_vars.sum()), 72
+    x = H.device_cands(synth.uniform_values(n, B, seed=61), B)
+    d = synth.normal_values(n, B, seed=62)
+    loss = _abi.gs_forward(prob, x)
+    grad = _abi.gs_backward(prob, x)
+    unsat, best = _abi.gs_round_check(prob, H.device_cands(d, B))
+    torch.cuda.synchronize()
+    xh = H.host64(x)
+    off = 0
+    for i, p in enumerate(parts):
+        rows = slice(off, off + p.n_vars)
+        lu, _ = oracle.forward(p.n_vars, p.clause_ptr, p.lits, xh[rows])
+        g_ref, scale = oracle.backward(p.n_vars, p.clause_ptr, p.lits, xh[rows])
+        _, u_ref, b_ref = oracle.round_check(p.n_vars, p.clause_ptr, p.lits, d[rows].astype(np.float64))
+        H.assert_loss(loss.cpu().numpy()[i], lu, "instance %d loss" % i)
+        H.assert_grad(H.host64(grad)[rows], g_ref, scale, "instance %d grad" % i)
+        assert np.array_equal(unsat.cpu().numpy()[i], u_ref)
+        assert int(best.cpu().numpy()[i]) == b_ref
+        off += p.n_vars
+
+
+def test_deterministic_bitwise():
+    cnf, prob = get("mixed")
+    B = 128
+    outs = []
+    for _ in range(2):
+        e = Engine(prob, B, "f32", seed=5)
+        for _ in range(3):
+            e.step()
+        torch.cuda.synchronize()
+        outs.append((e.delta.cpu().clone(), e.loss.cpu().clone(), e.unsat.cpu().clone()))
+    for a, b in zip(*outs):
+        assert torch.equal(a, b)
+
+
+def test_engine_graph_equals_eager():
+    cnf, prob = get("3sat")
+    B = 64
+    e1, e2 = Engine(prob, B, seed=2), Engine(prob, B, seed=2)
+    for _ in range(6):
+        e1.step()
+    e2.run(6, graph=True)
+    torch.cuda.synchronize()
+    assert torch.equal(e1.delta, e2.delta) and torch.equal(e1.loss, e2.loss) and torch.equal(e1.unsat, e2.unsat)
+
+
+def test_columns_beyond_B_untouched():
+    cnf, prob = get("edge")
+    n, B = cnf.n_vars, 13
+    full = torch.full((n, 16), 7.0, device="cuda")
+    delta = full[:, :B]
+    delta.copy_(H.device_cands(synth.init_delta(n, B, seed=1), B))
+    mfull, vfull = torch.full((n, 16), 7.0, device="cuda"), torch.full((n, 16), 7.0, device="cuda")
+    m, v = mfull[:, :B], vfull[:, :B]
+    m.zero_()
+    v.zero_()
+    xin = H.device_cands(synth.uniform_values(n, B, seed=2), B)
+    xfull = torch.full((n, 16), 7.0, device="cuda")
+    _abi.gs_step(prob, delta, m, v, 1, x_in=xin, x_out=xfull[:, :B])
+    g = torch.full((n, 16), 7.0, device="cuda")
+    _abi.gs_backward(prob, xin, grad=g[:, :B])
+    torch.cuda.synchronize()
+    for t in (full, mfull, vfull, xfull, g):
+        assert torch.all(t[:, B:] == 7.0)
+
+
+def test_wait_timeout_is_reported_and_context_survives():
+    cnf, prob = get("edge")
+    _abi.gs_wait_selftest(prob, limit_us=2000)
+    with pytest.raises(_abi.GSError) as ei:
+        _abi.gs_sync_status(prob)
+    assert ei.value.status == 6
+    _abi.gs_sync_status(prob)                 # cleared
+    x = H.device_cands(synth.uniform_values(cnf.n_vars, 8, seed=1), 8)
+    loss = _abi.gs_forward(prob, x)           # the context is still usable
+    torch.cuda.synchronize()
+    lu, _ = oracle.forward(cnf.n_vars, cnf.clause_ptr, cnf.lits, H.host64(x))
+    H.assert_loss(loss.cpu().numpy()[0], lu)
+
+
+def test_capture_without_reserve_is_refused():
+    cnf = synth.planted_ksat(200, 800, 3, seed=77)
+    prob = H.load(cnf)
+    x = H.device_cands(synth.uniform_values(200, 48, seed=1), 48)
+    g = torch.cuda.CUDAGraph()
+    s = torch.cuda.Stream()
+    with pytest.raises(_abi.GSError) as ei:
+        with torch.cuda.graph(g, stream=s):
+            _abi.gs_forward(prob, x)
+    assert ei.value.status == 7
