@@ -165,6 +165,30 @@ gs_status gs_forward(gs_problem* prob, const void* x, gs_dtype dtype, int32_t B,
                      gs_stream stream);
 
 /*
+ * gs_forward_noalloc - gs_forward for callers that must not allocate device memory. Some host
+ * programs cannot call cudaMalloc while they run: a process whose device memory is entirely
+ * pre-reserved by another allocator (a serving stack or framework caching allocator), code that
+ * runs while another component is capturing or replaying work on the device, or a latency-bound
+ * loop that cannot afford the device-wide synchronisation an allocation may cause. gs_forward
+ * may grow the problem's workspace on first use; this variant never allocates or frees memory.
+ * (The paper has no counterpart: this is an operational variant of the forward of Eq. 2 + Eq. 5.)
+ *   Arguments, output and arithmetic are those of gs_forward; results are identical.
+ *   Scratch: a fixed 16 MiB device array inside the library (plus a 256-byte counter), present
+ *   on every GPU that loads the library until the process exits. It holds the per-tile partial
+ *   sums, n_fwd_tiles (gs_info) x Bpad x 4 bytes, where Bpad is B rounded up to the candidate
+ *   chunk: a multiple of 128 (float32) or 256 (16-bit) once B exceeds that, else the next power
+ *   of two of at least 16 (float32) or 32 (16-bit). Larger requests are rejected with
+ *   GS_ERR_UNSUPPORTED and a message.
+ *   The first call on a device looks up the array's device address (with that device current);
+ *   make that first call before any stream capture. All calls on a device share the array and
+ *   leave their partials in it: calls that overlap on the GPU (other streams, other problems,
+ *   other host threads) race and must be serialised by the caller.
+ * Errors: as gs_forward, plus GS_ERR_UNSUPPORTED when the partials exceed the scratch.
+ */
+gs_status gs_forward_noalloc(gs_problem* prob, const void* x, gs_dtype dtype, int32_t B, int64_t ldB, double* loss,
+                             gs_stream stream);
+
+/*
  * gs_backward - gradient of the loss above with respect to x (back-propagation through
  * Eq. 2; the paper's dashed backward arrows):
  *   grad[v][b] = w_b * sum over occurrences (t, i) of v of  sign_i * prod_{j in t, j != i} f_j,

@@ -27,7 +27,7 @@ STATUS_NAMES = {
 # Every symbol include/gs.h declares.
 EXPORTED = (
     "gs_adam_default", "gs_load_cnf", "gs_load_batch", "gs_load_dimacs", "gs_inspect_cnf", "gs_info_get",
-    "gs_reserve", "gs_relax", "gs_forward", "gs_backward", "gs_step", "gs_round_check", "gs_check_bits",
+    "gs_reserve", "gs_relax", "gs_forward", "gs_forward_noalloc", "gs_backward", "gs_step", "gs_round_check", "gs_check_bits",
     "gs_wait_selftest", "gs_sync_status", "gs_free", "gs_status_str", "gs_last_error",
 )
 
@@ -86,6 +86,7 @@ def lib():
             "gs_reserve": (ctypes.c_int, [vp, i32, ctypes.c_int]),
             "gs_relax": (ctypes.c_int, [vp, vp, vp, ctypes.c_int, i32, i64, ctypes.c_float, vp]),
             "gs_forward": (ctypes.c_int, [vp, vp, ctypes.c_int, i32, i64, vp, vp]),
+            "gs_forward_noalloc": (ctypes.c_int, [vp, vp, ctypes.c_int, i32, i64, vp, vp]),
             "gs_backward": (ctypes.c_int, [vp, vp, ctypes.c_int, i32, i64, vp, vp, vp]),
             "gs_step": (ctypes.c_int, [vp, vp, vp, vp, vp, vp, vp, ctypes.c_int, i32, i64, i64,
                                        ctypes.POINTER(GsAdam), vp, vp, vp]),
@@ -269,6 +270,15 @@ def gs_forward(prob: Problem, x, loss=None, stream=None):
     if loss is None:
         loss = torch.empty((prob.n_inst, B), dtype=torch.float64, device=x.device)
     _check(lib().gs_forward(prob.handle, _ptr(x), _dtype_code(x), B, ldB, _ptr(loss), _stream(stream)), "gs_forward")
+    return loss
+
+
+def gs_forward_noalloc(prob: Problem, x, loss, stream=None):
+    """gs_forward for callers that must not allocate: ``loss`` (float64 [n_inst, B]) is required,
+    and the library's fixed scratch replaces the workspace (see include/gs.h)."""
+    B, ldB = _cand(x, "x", prob.n_vars)
+    _check(lib().gs_forward_noalloc(prob.handle, _ptr(x), _dtype_code(x), B, ldB, _ptr(loss), _stream(stream)),
+           "gs_forward_noalloc")
     return loss
 
 

@@ -7,6 +7,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -952,3 +953,81 @@ void gs_free(gs_problem* p) {
 }
 
 }  // extern "C"
+
+// =============================================================================================
+// Allocation-free forward (gs_forward_noalloc). The per-tile loss partials and the work-queue
+// counter that gs_forward keeps in the problem's workspace live here in one fixed device array
+// instead, so a call never allocates. The array is shared by every call on a device and keeps
+// the last call's contents; the counter is cleared by each call and the partials are fully
+// rewritten before they are read.
+namespace {
+
+constexpr size_t kNoAllocHeader = 256;                   // work-queue counter (int32 at offset 0)
+constexpr size_t kNoAllocPartialBytes = size_t(16) << 20; // 16 MiB of float32 tile partials
+constexpr int kNoAllocMaxDevices = 64;
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocHeader + kNoAllocPartialBytes];
+
+// Device address of g_noalloc_scratch per device, looked up once with that device current.
+void* g_noalloc_addr[kNoAllocMaxDevices] = {};
+std::mutex g_noalloc_mu;
+
+gs_status noalloc_scratch(int device, unsigned char** out) {
+    if (device < 0 || device >= kNoAllocMaxDevices) return fail(GS_ERR_UNSUPPORTED, "device index beyond 63");
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_addr[device]) {
+        void* ptr = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+        if (e != cudaSuccess || !ptr) return cuda_fail(e, "cudaGetSymbolAddress of the no-alloc scratch");
+        g_noalloc_addr[device] = ptr;
+    }
+    *out = static_cast<unsigned char*>(g_noalloc_addr[device]);
+    return GS_OK;
+}
+
+}  // namespace
+
+extern "C" gs_status gs_forward_noalloc(gs_problem* p, const void* x, gs_dtype dtype, int32_t B, int64_t ldB,
+                                        double* loss, gs_stream stream) {
+    if (!p) return fail(GS_ERR_INVALID_ARG, "null problem");
+    gs_status st;
+    if ((st = check_batch(p, dtype, B, ldB)) != GS_OK) return st;
+    if ((st = need_ptr(x, "x", p->h.n > 0 && B > 0)) != GS_OK) return st;
+    if (B > 0 && !loss) return fail(GS_ERR_INVALID_ARG, "null loss");
+    if (loss && (reinterpret_cast<uintptr_t>(loss) & 7u)) return fail(GS_ERR_INVALID_ARG, "loss misaligned");
+    if ((st = check_device(p)) != GS_OK) return st;
+    if (B == 0) return GS_OK;
+    const Chunking c = chunking_for(dtype, B);
+    const size_t need = static_cast<size_t>(p->n_fitems) * static_cast<size_t>(c.bpad) * sizeof(float);
+    if (need > kNoAllocPartialBytes)
+        return fail(GS_ERR_UNSUPPORTED, "gs_forward_noalloc needs " + std::to_string(need) +
+                                            " bytes of tile partials (clause tiles x padded B x 4); its fixed "
+                                            "scratch holds 16 MiB - use gs_forward for this size");
+    unsigned char* base = nullptr;
+    if ((st = noalloc_scratch(p->device, &base)) != GS_OK) return st;
+    int32_t* head = reinterpret_cast<int32_t*>(base);
+    float* part = reinterpret_cast<float*>(base + kNoAllocHeader);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    FwdParams fp{};
+    fp.items = p->fitems;
+    fp.n_items = p->n_fitems;
+    fp.n_chunks = c.n_chunks;
+    fp.B = B;
+    fp.bpad = c.bpad;
+    fp.ldB = ldB;
+    fp.codes = p->fcodes;
+    fp.ctab = p->fctab;
+    fp.x = x;
+    fp.loss_part = part;
+    fp.head = head;
+    fp.status = p->status;
+    GS_CUDA(cudaMemsetAsync(head, 0, sizeof(int32_t), s), "memset no-alloc counter");
+    const int64_t total = static_cast<int64_t>(fp.n_items) * c.n_chunks;
+    if (total > 0) {
+        const int grid = static_cast<int>(std::min<int64_t>(grid_forward(dtype, c.lc), total));
+        GS_CUDA(launch_forward(fp, dtype, c.lc, grid, s), "forward launch");
+    }
+    GS_CUDA(launch_loss_reduce(part, c.bpad, p->f_iptr, p->f_list, p->inst_empty, p->h.n_inst, B, loss, s),
+            "loss reduce launch");
+    return GS_OK;
+}
