@@ -42,6 +42,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle sample")
+    ap.add_argument("--var-lanes", type=int, default=0, help="cap on lanes per candidate chunk (gs_set_tuning)")
     return ap.parse_args()
 
 
@@ -205,6 +206,8 @@ def run_native(args):
 
     cnf, B, dtype, desc = workload_setup(args.workload, args.dtype)
     prob = _abi.gs_load_cnf(cnf.n_vars, cnf.clause_ptr, cnf.lits)
+    if args.var_lanes:
+        _abi.gs_set_tuning(prob, var_lanes=args.var_lanes)
     info = prob.info()
     eng = Engine(prob, B, dtype, seed=1000 * rank + 1)
     nnz, n = cnf.nnz, cnf.n_vars
@@ -252,7 +255,8 @@ def run_native(args):
     value = evals_per_step * K * world / (total_ms / 1000.0)
     # roofline of the dominant kernel (fused variable-major pass inside gs_step)
     peak, peak_kind = measured_peaks()
-    n_chunks = -(-B // (32 * (16 // s_bytes)))
+    lanes = args.var_lanes or 32
+    n_chunks = -(-B // (lanes * (16 // s_bytes)))
     compulsory = n * B * (24 + 2 * s_bytes) + n * ((B + 63) // 64) * 8 + n_chunks * 4 * (
         info["n_occ_codes"] + info["n_var_tiles"] * 16)
     gather_model = nnz * B * 2 * s_bytes + n * B * (24 + s_bytes)
@@ -318,7 +322,7 @@ def run_native(args):
                    "parallelism": "dp%d (independent candidate batches)" % world,
                    "l2": "inputs larger than L2: x %.0f MB + delta/m/v %.0f MB per step" % (
                        n * B * s_bytes / 1e6, n * B * 12 / 1e6),
-                   "steps_per_s": 1000.0 * K / total_ms},
+                   "steps_per_s": 1000.0 * K / total_ms, "var_lanes": args.var_lanes or 32},
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "gpu_launches": 4 * K,
     }
     if rank == 0:

@@ -145,6 +145,25 @@ gs_status gs_info_get(const gs_problem* prob, gs_info* out);
 gs_status gs_reserve(gs_problem* prob, int32_t B, gs_dtype dtype);
 
 /*
+ * Tuning of the tiled kernels. Each lane handles 4 (float32) or 8 (16-bit) consecutive
+ * candidates and a candidate chunk spans up to `lanes` lanes; the kernels sweep all tiles once
+ * per chunk, so the rows of relaxed values gathered during a sweep are n x chunk wide. A
+ * smaller cap keeps that working set inside L2 at the price of more sweeps over the tiles.
+ *   var_lanes  cap for the variable-major pass (gs_backward, gs_step): 0 (= 32), 4, 8, 16, 32.
+ *   fwd_lanes  cap for the clause-major forward (gs_forward): 0 (= 32), 4, 8, 16, 32.
+ * Results do not depend on the tuning beyond float32 summation order. Call gs_reserve again
+ * after changing it if later calls are captured in a CUDA graph.
+ */
+typedef struct {
+    int32_t var_lanes;
+    int32_t fwd_lanes;
+} gs_tuning;
+
+/* gs_set_tuning / gs_get_tuning - set or read the caps above. Errors: GS_ERR_INVALID_ARG. */
+gs_status gs_set_tuning(gs_problem* prob, const gs_tuning* tuning);
+gs_status gs_get_tuning(const gs_problem* prob, gs_tuning* tuning);
+
+/*
  * gs_relax - relaxed values x = sigma(delta / tau) (Eq. 3 with two states and no Gumbel
  * noise), rounded to nearest-even when dtype is 16-bit.
  *   delta  device float [n][ldB] (input).   x  device dtype [n][ldB] (output).

@@ -27,7 +27,7 @@ STATUS_NAMES = {
 # Every symbol include/gs.h declares.
 EXPORTED = (
     "gs_adam_default", "gs_load_cnf", "gs_load_batch", "gs_load_dimacs", "gs_inspect_cnf", "gs_info_get",
-    "gs_reserve", "gs_relax", "gs_forward", "gs_forward_noalloc", "gs_backward", "gs_step", "gs_round_check", "gs_check_bits",
+    "gs_set_tuning", "gs_get_tuning", "gs_reserve", "gs_relax", "gs_forward", "gs_forward_noalloc", "gs_backward", "gs_step", "gs_round_check", "gs_check_bits",
     "gs_wait_selftest", "gs_sync_status", "gs_free", "gs_status_str", "gs_last_error",
 )
 
@@ -51,6 +51,10 @@ class GsInfo(ctypes.Structure):
 
     def as_dict(self) -> dict:
         return {name: int(getattr(self, name)) for name, _ in self._fields_}
+
+
+class GsTuning(ctypes.Structure):
+    _fields_ = [("var_lanes", ctypes.c_int32), ("fwd_lanes", ctypes.c_int32)]
 
 
 class GsAdam(ctypes.Structure):
@@ -83,6 +87,8 @@ def lib():
             "gs_load_dimacs": (ctypes.c_int, [cp, vp, pp]),
             "gs_inspect_cnf": (ctypes.c_int, [i64, i64, vp, vp, ctypes.POINTER(GsInfo)]),
             "gs_info_get": (ctypes.c_int, [vp, ctypes.POINTER(GsInfo)]),
+            "gs_set_tuning": (ctypes.c_int, [vp, ctypes.POINTER(GsTuning)]),
+            "gs_get_tuning": (ctypes.c_int, [vp, ctypes.POINTER(GsTuning)]),
             "gs_reserve": (ctypes.c_int, [vp, i32, ctypes.c_int]),
             "gs_relax": (ctypes.c_int, [vp, vp, vp, ctypes.c_int, i32, i64, ctypes.c_float, vp]),
             "gs_forward": (ctypes.c_int, [vp, vp, ctypes.c_int, i32, i64, vp, vp]),
@@ -247,6 +253,17 @@ def gs_inspect_cnf(n_vars: int, clause_ptr, lits) -> dict:
 
 def gs_info_get(prob: Problem) -> dict:
     return prob.info()
+
+
+def gs_set_tuning(prob: Problem, var_lanes: int = 0, fwd_lanes: int = 0) -> None:
+    t = GsTuning(int(var_lanes), int(fwd_lanes))
+    _check(lib().gs_set_tuning(prob.handle, ctypes.byref(t)), "gs_set_tuning")
+
+
+def gs_get_tuning(prob: Problem) -> dict:
+    t = GsTuning()
+    _check(lib().gs_get_tuning(prob.handle, ctypes.byref(t)), "gs_get_tuning")
+    return {"var_lanes": int(t.var_lanes), "fwd_lanes": int(t.fwd_lanes)}
 
 
 def gs_reserve(prob: Problem, B: int, dtype) -> None:

@@ -338,12 +338,14 @@ gs_status upload(const std::vector<T>& h, T** d, int64_t* bytes, cudaStream_t s)
     return GS_OK;
 }
 
-Chunking chunking_for(int dtype, int32_t B) {
+// lc_max (4, 8, 16 or 32) caps the lanes per candidate chunk: smaller chunks keep a smaller
+// set of relaxed-value rows resident in L2 at the price of more passes over the tiles.
+Chunking chunking_for(int dtype, int32_t B, int lc_max = 32) {
     Chunking c{};
     c.vec = (dtype == kF32) ? 4 : 8;
     const int need = (B + c.vec - 1) / c.vec;
     c.lc = 4;
-    while (c.lc < need && c.lc < 32) c.lc *= 2;
+    while (c.lc < need && c.lc < lc_max) c.lc *= 2;
     c.bc = c.lc * c.vec;
     c.n_chunks = (B + c.bc - 1) / c.bc;
     if (c.n_chunks < 1) c.n_chunks = 1;
@@ -384,6 +386,9 @@ struct gs_problem {
     size_t split_cap = 0;
     uint64_t* bits = nullptr;
     size_t bits_cap = 0;         // words
+    // tuning: caps on the lanes per candidate chunk (gs_set_tuning)
+    int var_lc_max = 32;
+    int fwd_lc_max = 32;
 };
 
 namespace {
@@ -422,15 +427,17 @@ gs_status grow(T** ptr, size_t* cap, size_t need, cudaStream_t s, bool in_captur
 
 gs_status ensure_ws(gs_problem* p, int dtype, int32_t B, bool need_bits, cudaStream_t s) {
     const bool cap = capturing(s);
-    const Chunking c = chunking_for(dtype, B);
+    const Chunking cv = chunking_for(dtype, B, p->var_lc_max);
+    const Chunking cf = chunking_for(dtype, B, p->fwd_lc_max);
     const size_t items = static_cast<size_t>(std::max(p->n_fitems, p->n_vitems));
+    const size_t bpad = static_cast<size_t>(std::max(cv.bpad, cf.bpad));
     gs_status st;
-    if ((st = grow(&p->part, &p->part_cap, std::max<size_t>(1, items * c.bpad), s, cap, "loss partials")) != GS_OK)
+    if ((st = grow(&p->part, &p->part_cap, std::max<size_t>(1, items * bpad), s, cap, "loss partials")) != GS_OK)
         return st;
-    if ((st = grow(&p->split, &p->split_cap, std::max<size_t>(1, static_cast<size_t>(p->h.n_split_rows) * c.bpad), s,
+    if ((st = grow(&p->split, &p->split_cap, std::max<size_t>(1, static_cast<size_t>(p->h.n_split_rows) * cv.bpad), s,
                    cap, "split partials")) != GS_OK)
         return st;
-    if ((st = grow(&p->ctl, &p->ctl_cap, 4 + static_cast<size_t>(p->h.n_split) * c.n_chunks, s, cap, "counters")) !=
+    if ((st = grow(&p->ctl, &p->ctl_cap, 4 + static_cast<size_t>(p->h.n_split) * cv.n_chunks, s, cap, "counters")) !=
         GS_OK)
         return st;
     if (need_bits) {
@@ -598,7 +605,7 @@ gs_status var_pass(gs_problem* p, int mode, const void* x_in, int dtype, int32_t
                    uint64_t* bits, cudaStream_t s) {
     gs_status st;
     if ((st = ensure_ws(p, dtype, B, false, s)) != GS_OK) return st;
-    const Chunking c = chunking_for(dtype, B);
+    const Chunking c = chunking_for(dtype, B, p->var_lc_max);
     VarParams vp{};
     vp.items = p->vitems;
     vp.n_items = p->n_vitems;
@@ -761,6 +768,23 @@ gs_status gs_info_get(const gs_problem* p, gs_info* out) {
     return GS_OK;
 }
 
+gs_status gs_set_tuning(gs_problem* p, const gs_tuning* t) {
+    if (!p || !t) return fail(GS_ERR_INVALID_ARG, "null argument");
+    auto ok = [](int32_t l) { return l == 0 || l == 4 || l == 8 || l == 16 || l == 32; };
+    if (!ok(t->var_lanes) || !ok(t->fwd_lanes))
+        return fail(GS_ERR_INVALID_ARG, "lanes per candidate chunk must be 0, 4, 8, 16 or 32");
+    p->var_lc_max = t->var_lanes ? t->var_lanes : 32;
+    p->fwd_lc_max = t->fwd_lanes ? t->fwd_lanes : 32;
+    return GS_OK;
+}
+
+gs_status gs_get_tuning(const gs_problem* p, gs_tuning* t) {
+    if (!p || !t) return fail(GS_ERR_INVALID_ARG, "null argument");
+    t->var_lanes = p->var_lc_max;
+    t->fwd_lanes = p->fwd_lc_max;
+    return GS_OK;
+}
+
 gs_status gs_reserve(gs_problem* p, int32_t B, gs_dtype dtype) {
     if (!p) return fail(GS_ERR_INVALID_ARG, "null problem");
     gs_status st = check_device(p);
@@ -770,10 +794,11 @@ gs_status gs_reserve(gs_problem* p, int32_t B, gs_dtype dtype) {
     if (st != GS_OK) return st;
     // First use of a kernel instantiation queries its occupancy and sets its shared-memory
     // attributes; do that here, outside any stream capture.
-    const Chunking c = chunking_for(dtype, B);
-    grid_var_pass(dtype, kModeGrad, c.lc);
-    grid_var_pass(dtype, kModeAdam, c.lc);
-    grid_forward(dtype, c.lc);
+    const Chunking cv = chunking_for(dtype, B, p->var_lc_max);
+    const Chunking cf = chunking_for(dtype, B, p->fwd_lc_max);
+    grid_var_pass(dtype, kModeGrad, cv.lc);
+    grid_var_pass(dtype, kModeAdam, cv.lc);
+    grid_forward(dtype, cf.lc);
     grid_check(lanes_for_words(nwords(B)));
     GS_CUDA(cudaDeviceSynchronize(), "cudaDeviceSynchronize");
     return GS_OK;
@@ -805,7 +830,7 @@ gs_status gs_forward(gs_problem* p, const void* x, gs_dtype dtype, int32_t B, in
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     if (B == 0) return GS_OK;
     if ((st = ensure_ws(p, dtype, B, false, s)) != GS_OK) return st;
-    const Chunking c = chunking_for(dtype, B);
+    const Chunking c = chunking_for(dtype, B, p->fwd_lc_max);
     FwdParams fp{};
     fp.items = p->fitems;
     fp.n_items = p->n_fitems;

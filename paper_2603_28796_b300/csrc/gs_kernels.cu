@@ -116,7 +116,56 @@ struct Elem<__half> {
     static constexpr int VEC = 8;
 };
 
-__device__ __forceinline__ uint4 ld_gather16(const void* p) { return __ldg(reinterpret_cast<const uint4*>(p)); }
+// L2 eviction policies: the gathered relaxed values of the current candidate chunk should stay
+// in L2 (evict_last) while the once-per-step state streams pass through it (evict_first).
+__device__ __forceinline__ uint64_t l2_evict_last() {
+    uint64_t p;
+    asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ uint64_t l2_evict_first() {
+    uint64_t p;
+    asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ uint4 ld_gather16(const void* p) {
+    uint4 r;
+    asm("ld.global.nc.L2::cache_hint.v4.u32 {%0, %1, %2, %3}, [%4], %5;"
+        : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w)
+        : "l"(p), "l"(l2_evict_last()));
+    return r;
+}
+__device__ __forceinline__ float4 ld_first_f4(const float* p) {
+    float4 r;
+    asm volatile("ld.global.L1::no_allocate.L2::cache_hint.v4.f32 {%0, %1, %2, %3}, [%4], %5;"
+                 : "=f"(r.x), "=f"(r.y), "=f"(r.z), "=f"(r.w)
+                 : "l"(p), "l"(l2_evict_first()));
+    return r;
+}
+__device__ __forceinline__ float2 ld_first_f2(const float* p) {
+    float2 r;
+    asm volatile("ld.global.L1::no_allocate.L2::cache_hint.v2.f32 {%0, %1}, [%2], %3;"
+                 : "=f"(r.x), "=f"(r.y)
+                 : "l"(p), "l"(l2_evict_first()));
+    return r;
+}
+__device__ __forceinline__ float ld_first_f1(const float* p) {
+    float r;
+    asm volatile("ld.global.L1::no_allocate.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(r) : "l"(p), "l"(l2_evict_first()));
+    return r;
+}
+__device__ __forceinline__ void st_first_u4(void* p, uint4 v) {
+    asm volatile("st.global.L2::cache_hint.v4.u32 [%0], {%1, %2, %3, %4}, %5;" ::"l"(p), "r"(v.x), "r"(v.y), "r"(v.z),
+                 "r"(v.w), "l"(l2_evict_first())
+                 : "memory");
+}
+__device__ __forceinline__ void st_first_u2(void* p, uint2 v) {
+    asm volatile("st.global.L2::cache_hint.v2.u32 [%0], {%1, %2}, %3;" ::"l"(p), "r"(v.x), "r"(v.y), "l"(l2_evict_first())
+                 : "memory");
+}
+__device__ __forceinline__ void st_first_u1(void* p, uint32_t v) {
+    asm volatile("st.global.L2::cache_hint.u32 [%0], %1, %2;" ::"l"(p), "r"(v), "l"(l2_evict_first()) : "memory");
+}
 
 template <typename T>
 __device__ __forceinline__ void unpack(const uint4& r, float* x);
@@ -169,18 +218,18 @@ __device__ __forceinline__ void ld_stream(const float* p, float* x) {
     if constexpr (N % 4 == 0) {
 #pragma unroll
         for (int k = 0; k < N / 4; ++k) {
-            const float4 t = __ldcs(reinterpret_cast<const float4*>(p) + k);
+            const float4 t = ld_first_f4(p + 4 * k);
             x[4 * k] = t.x;
             x[4 * k + 1] = t.y;
             x[4 * k + 2] = t.z;
             x[4 * k + 3] = t.w;
         }
     } else if constexpr (N == 2) {
-        const float2 t = __ldcs(reinterpret_cast<const float2*>(p));
+        const float2 t = ld_first_f2(p);
         x[0] = t.x;
         x[1] = t.y;
     } else {
-        x[0] = __ldcs(p);
+        x[0] = ld_first_f1(p);
     }
 }
 template <int N>
@@ -188,11 +237,12 @@ __device__ __forceinline__ void st_stream(float* p, const float* x) {
     if constexpr (N % 4 == 0) {
 #pragma unroll
         for (int k = 0; k < N / 4; ++k)
-            __stcs(reinterpret_cast<float4*>(p) + k, make_float4(x[4 * k], x[4 * k + 1], x[4 * k + 2], x[4 * k + 3]));
+            st_first_u4(p + 4 * k, make_uint4(__float_as_uint(x[4 * k]), __float_as_uint(x[4 * k + 1]),
+                                              __float_as_uint(x[4 * k + 2]), __float_as_uint(x[4 * k + 3])));
     } else if constexpr (N == 2) {
-        __stcs(reinterpret_cast<float2*>(p), make_float2(x[0], x[1]));
+        st_first_u2(p, make_uint2(__float_as_uint(x[0]), __float_as_uint(x[1])));
     } else {
-        __stcs(p, x[0]);
+        st_first_u1(p, __float_as_uint(x[0]));
     }
 }
 // N consecutive values of T from floats (round to nearest even for 16-bit types).
@@ -210,11 +260,11 @@ __device__ __forceinline__ void st_vals(T* p, const float* x) {
                    (static_cast<uint32_t>(*reinterpret_cast<const uint16_t*>(&hi)) << 16);
         }
         if constexpr (N == 8) {
-            __stcs(reinterpret_cast<uint4*>(p), make_uint4(w[0], w[1], w[2], w[3]));
+            st_first_u4(p, make_uint4(w[0], w[1], w[2], w[3]));
         } else if constexpr (N == 4) {
-            __stcs(reinterpret_cast<uint2*>(p), make_uint2(w[0], w[1]));
+            st_first_u2(p, make_uint2(w[0], w[1]));
         } else if constexpr (N == 2) {
-            __stcs(reinterpret_cast<unsigned int*>(p), w[0]);
+            st_first_u1(p, w[0]);
         } else {
             *p = from_f32<T>(x[0]);
         }
@@ -232,7 +282,7 @@ __device__ __forceinline__ void kahan_add(float& s, float& c, float x) {
 // sigma(-|z|) = e / (1 + e).
 __device__ __forceinline__ float sigmoid(float z) {
     const float e = expf(-fabsf(z));
-    const float r = 1.0f / (1.0f + e);
+    const float r = __frcp_rn(1.0f + e);
     return z >= 0.0f ? r : e * r;
 }
 
@@ -241,13 +291,13 @@ __device__ __forceinline__ float sigmoid(float z) {
 __device__ __forceinline__ void adam_update(float gx, float& d, float& m, float& v, float& x_new, const AdamK& k) {
     const float z = d * k.inv_tau;
     const float e = expf(-fabsf(z));
-    const float r = 1.0f / (1.0f + e);
+    const float r = __frcp_rn(1.0f + e);
     const float q = e * r;
     const float g = gx * (r * q) * k.inv_tau;
     m = fmaf(k.beta1, m, k.one_minus_beta1 * g);
     v = fmaf(k.beta2, v, k.one_minus_beta2 * (g * g));
     const float den = sqrtf(v) * k.inv_sqrt_bc2 + k.eps;
-    d = d - k.step_size * (m / den);
+    d = d - k.step_size * (m * __frcp_rn(den));
     x_new = sigmoid(d * k.inv_tau);
 }
 
@@ -335,7 +385,67 @@ __device__ __forceinline__ void var_slots(const uint32_t* cd, int cs, int ce, co
 
 // Fixed-width occurrence loop: every occurrence in [cs, ce) has exactly K codes (all clauses
 // of the tile have width K + 1, e.g. the paper's width-3 normal form with K = 2). OB whole
-// occurrences per batch, their K * OB gathers issued together.
+// occurrences per batch, their K * OB gathers issued together; full batches run without
+// per-slot predicates, the last partial batch with them.
+template <int K>
+__device__ __forceinline__ void fixed_ab(uint32_t c, float& a, float& b) {
+    if constexpr (K == 1) {
+        code_ab(c, a, b);   // unit-clause sentinels only occur in K = 1 tiles
+    } else {
+        const uint32_t pos = ~c & 1u;                        // 1 for a positive literal
+        a = __uint_as_float(0x3f800000u | (pos << 31));    // -1 positive, +1 negated
+        b = __uint_as_float(pos * 0x3f800000u);            //  1 positive,  0 negated
+    }
+}
+
+template <typename T, int VEC, int K, int OB, bool LOSS, bool TAIL>
+__device__ __forceinline__ void occ_batch(const uint32_t* cd, int s, int ce, const T* xcol, int64_t ldB, bool ld_ok,
+                                          float2 (&G2)[VEC / 2], float (&Ls)[VEC], float (&Lc)[VEC],
+                                          const float (&xs)[VEC]) {
+    constexpr int H = VEC / 2;
+    constexpr int NS = OB * K;
+    uint32_t cw[NS];
+    uint4 raw[NS];
+#pragma unroll
+    for (int j = 0; j < NS; ++j) cw[j] = (!TAIL || s + j < ce) ? cd[s + j] : (kVSentinel << kVShift);
+#pragma unroll
+    for (int j = 0; j < NS; ++j) {
+        raw[j] = make_uint4(0u, 0u, 0u, 0u);
+        const uint32_t u = cw[j] >> kVShift;
+        const bool load = ld_ok && ((K > 1 && !TAIL) || u != kVSentinel);
+        if (load) raw[j] = ld_gather16(xcol + static_cast<int64_t>(u) * ldB);
+    }
+#pragma unroll
+    for (int o = 0; o < OB; ++o) {
+        float2 prod[H];
+#pragma unroll
+        for (int j = 0; j < K; ++j) {
+            float xv[VEC];
+            unpack<T>(raw[o * K + j], xv);
+            float a, b;
+            fixed_ab<(TAIL ? 1 : K)>(cw[o * K + j], a, b);
+#pragma unroll
+            for (int h = 0; h < H; ++h) {
+                const float2 f = __ffma2_rn(dup2(a), make_float2(xv[2 * h], xv[2 * h + 1]), dup2(b));
+                prod[h] = (j == 0) ? f : __fmul2_rn(prod[h], f);
+            }
+        }
+        const uint32_t last = cw[o * K + K - 1];
+        const bool valid = !TAIL || (s + o * K) < ce;
+        const float sg = valid ? ((last & kVSelfNeg) ? 1.0f : -1.0f) : 0.0f;
+#pragma unroll
+        for (int h = 0; h < H; ++h) G2[h] = __ffma2_rn(dup2(sg), prod[h], G2[h]);
+        if (LOSS && valid && (last & kVCredit)) {
+            const bool sneg = (last & kVSelfNeg) != 0u;
+#pragma unroll
+            for (int h = 0; h < H; ++h) {
+                kahan_add(Ls[2 * h], Lc[2 * h], (sneg ? xs[2 * h] : 1.0f - xs[2 * h]) * prod[h].x);
+                kahan_add(Ls[2 * h + 1], Lc[2 * h + 1], (sneg ? xs[2 * h + 1] : 1.0f - xs[2 * h + 1]) * prod[h].y);
+            }
+        }
+    }
+}
+
 template <typename T, int VEC, int K, bool LOSS>
 __device__ __forceinline__ void var_occ_fixed(const uint32_t* cd, int cs, int ce, const T* xcol, int64_t ldB,
                                               bool ld_ok, float (&gacc)[VEC], float (&Ls)[VEC], float (&Lc)[VEC],
@@ -346,47 +456,10 @@ __device__ __forceinline__ void var_occ_fixed(const uint32_t* cd, int cs, int ce
     float2 G2[H];
 #pragma unroll
     for (int h = 0; h < H; ++h) G2[h] = make_float2(gacc[2 * h], gacc[2 * h + 1]);
-    for (int s = cs; s < ce; s += NS) {
-        uint32_t cw[NS];
-        uint4 raw[NS];
-#pragma unroll
-        for (int j = 0; j < NS; ++j) cw[j] = (s + j < ce) ? cd[s + j] : (kVSentinel << kVShift);
-#pragma unroll
-        for (int j = 0; j < NS; ++j) {
-            const uint32_t u = cw[j] >> kVShift;
-            raw[j] = make_uint4(0u, 0u, 0u, 0u);
-            if (ld_ok && u != kVSentinel) raw[j] = ld_gather16(xcol + static_cast<int64_t>(u) * ldB);
-        }
-#pragma unroll
-        for (int o = 0; o < OB; ++o) {
-            float2 prod[H];
-#pragma unroll
-            for (int j = 0; j < K; ++j) {
-                float xv[VEC];
-                unpack<T>(raw[o * K + j], xv);
-                float a, b;
-                code_ab(cw[o * K + j], a, b);
-#pragma unroll
-                for (int h = 0; h < H; ++h) {
-                    const float2 f = __ffma2_rn(dup2(a), make_float2(xv[2 * h], xv[2 * h + 1]), dup2(b));
-                    prod[h] = (j == 0) ? f : __fmul2_rn(prod[h], f);
-                }
-            }
-            const uint32_t last = cw[o * K + K - 1];
-            const bool valid = (s + o * K) < ce;
-            const float sg = valid ? ((last & kVSelfNeg) ? 1.0f : -1.0f) : 0.0f;
-#pragma unroll
-            for (int h = 0; h < H; ++h) G2[h] = __ffma2_rn(dup2(sg), prod[h], G2[h]);
-            if (LOSS && valid && (last & kVCredit)) {
-                const bool sneg = (last & kVSelfNeg) != 0u;
-#pragma unroll
-                for (int h = 0; h < H; ++h) {
-                    kahan_add(Ls[2 * h], Lc[2 * h], (sneg ? xs[2 * h] : 1.0f - xs[2 * h]) * prod[h].x);
-                    kahan_add(Ls[2 * h + 1], Lc[2 * h + 1], (sneg ? xs[2 * h + 1] : 1.0f - xs[2 * h + 1]) * prod[h].y);
-                }
-            }
-        }
-    }
+    int s = cs;
+    for (; s + NS <= ce; s += NS)
+        occ_batch<T, VEC, K, OB, LOSS, false>(cd, s, ce, xcol, ldB, ld_ok, G2, Ls, Lc, xs);
+    if (s < ce) occ_batch<T, VEC, K, OB, LOSS, true>(cd, s, ce, xcol, ldB, ld_ok, G2, Ls, Lc, xs);
 #pragma unroll
     for (int h = 0; h < H; ++h) {
         gacc[2 * h] = G2[h].x;
