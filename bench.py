@@ -43,6 +43,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle sample")
     ap.add_argument("--var-lanes", type=int, default=0, help="cap on lanes per candidate chunk (gs_set_tuning)")
+    ap.add_argument("--var-gather", type=int, default=0, help="0: automatic, 1: register loads, 2: TMA gather4 ring (gs_set_tuning)")
     return ap.parse_args()
 
 
@@ -206,8 +207,8 @@ def run_native(args):
 
     cnf, B, dtype, desc = workload_setup(args.workload, args.dtype)
     prob = _abi.gs_load_cnf(cnf.n_vars, cnf.clause_ptr, cnf.lits)
-    if args.var_lanes:
-        _abi.gs_set_tuning(prob, var_lanes=args.var_lanes)
+    if args.var_lanes or args.var_gather:
+        _abi.gs_set_tuning(prob, var_lanes=args.var_lanes, var_gather=args.var_gather)
     info = prob.info()
     eng = Engine(prob, B, dtype, seed=1000 * rank + 1)
     nnz, n = cnf.nnz, cnf.n_vars
@@ -322,7 +323,8 @@ def run_native(args):
                    "parallelism": "dp%d (independent candidate batches)" % world,
                    "l2": "inputs larger than L2: x %.0f MB + delta/m/v %.0f MB per step" % (
                        n * B * s_bytes / 1e6, n * B * 12 / 1e6),
-                   "steps_per_s": 1000.0 * K / total_ms, "var_lanes": args.var_lanes or 32},
+                   "steps_per_s": 1000.0 * K / total_ms, "var_lanes": args.var_lanes or 32,
+                   "var_gather": "tma_gather4" if args.var_gather == 2 else "registers"},
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "gpu_launches": 4 * K,
     }
     if rank == 0:

@@ -151,12 +151,17 @@ gs_status gs_reserve(gs_problem* prob, int32_t B, gs_dtype dtype);
  * smaller cap keeps that working set inside L2 at the price of more sweeps over the tiles.
  *   var_lanes  cap for the variable-major pass (gs_backward, gs_step): 0 (= 32), 4, 8, 16, 32.
  *   fwd_lanes  cap for the clause-major forward (gs_forward): 0 (= 32), 4, 8, 16, 32.
+ *   var_gather how the variable-major pass fetches the rows its occurrence codes name:
+ *              0 = automatic (currently per-lane register loads), 1 = per-lane register loads,
+ *              2 = TMA tile::gather4 copies into a shared-memory ring when a chunk spans 32
+ *              lanes (register loads otherwise).
  * Results do not depend on the tuning beyond float32 summation order. Call gs_reserve again
  * after changing it if later calls are captured in a CUDA graph.
  */
 typedef struct {
     int32_t var_lanes;
     int32_t fwd_lanes;
+    int32_t var_gather;
 } gs_tuning;
 
 /* gs_set_tuning / gs_get_tuning - set or read the caps above. Errors: GS_ERR_INVALID_ARG. */

@@ -54,7 +54,7 @@ class GsInfo(ctypes.Structure):
 
 
 class GsTuning(ctypes.Structure):
-    _fields_ = [("var_lanes", ctypes.c_int32), ("fwd_lanes", ctypes.c_int32)]
+    _fields_ = [("var_lanes", ctypes.c_int32), ("fwd_lanes", ctypes.c_int32), ("var_gather", ctypes.c_int32)]
 
 
 class GsAdam(ctypes.Structure):
@@ -255,15 +255,15 @@ def gs_info_get(prob: Problem) -> dict:
     return prob.info()
 
 
-def gs_set_tuning(prob: Problem, var_lanes: int = 0, fwd_lanes: int = 0) -> None:
-    t = GsTuning(int(var_lanes), int(fwd_lanes))
+def gs_set_tuning(prob: Problem, var_lanes: int = 0, fwd_lanes: int = 0, var_gather: int = 0) -> None:
+    t = GsTuning(int(var_lanes), int(fwd_lanes), int(var_gather))
     _check(lib().gs_set_tuning(prob.handle, ctypes.byref(t)), "gs_set_tuning")
 
 
 def gs_get_tuning(prob: Problem) -> dict:
     t = GsTuning()
     _check(lib().gs_get_tuning(prob.handle, ctypes.byref(t)), "gs_get_tuning")
-    return {"var_lanes": int(t.var_lanes), "fwd_lanes": int(t.fwd_lanes)}
+    return {"var_lanes": int(t.var_lanes), "fwd_lanes": int(t.fwd_lanes), "var_gather": int(t.var_gather)}
 
 
 def gs_reserve(prob: Problem, B: int, dtype) -> None:

@@ -1,5 +1,7 @@
 // Host side of the C ABI (include/gs.h): validation, the clause->literal and var->occurrence
 // tile builders, device upload, workspace, and dispatch to the kernels in gs_kernels.cu.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -386,9 +388,15 @@ struct gs_problem {
     size_t split_cap = 0;
     uint64_t* bits = nullptr;
     size_t bits_cap = 0;         // words
-    // tuning: caps on the lanes per candidate chunk (gs_set_tuning)
+    uint16_t* part16 = nullptr;  // per-tile unsat counts
+    size_t part16_cap = 0;
+    double* stage = nullptr;     // stage-1 sums of the tile reductions (double or int32)
+    size_t stage_cap = 0;        // doubles
+    int sms = 148;
+    // tuning: caps on the lanes per candidate chunk, gather mode (gs_set_tuning)
     int var_lc_max = 32;
     int fwd_lc_max = 32;
+    int var_gather = 0;
 };
 
 namespace {
@@ -404,6 +412,13 @@ bool capturing(cudaStream_t s) {
     cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
     if (cudaStreamIsCapturing(s, &st) != cudaSuccess) return false;
     return st != cudaStreamCaptureStatusNone;
+}
+
+// Stage-1 segments of the tile reductions: enough blocks to fill the GPU a few times over.
+int32_t n_segments(const gs_problem* p, int32_t B) {
+    const int64_t slices = static_cast<int64_t>((std::max(B, 1) + 31) / 32) * std::max(p->h.n_inst, 1);
+    const int64_t want = (4LL * p->sms + slices - 1) / slices;
+    return static_cast<int32_t>(std::min<int64_t>(32, std::max<int64_t>(1, want)));
 }
 
 template <typename T>
@@ -445,6 +460,14 @@ gs_status ensure_ws(gs_problem* p, int dtype, int32_t B, bool need_bits, cudaStr
                        "bits")) != GS_OK)
             return st;
     }
+    if ((st = grow(&p->part16, &p->part16_cap,
+                   std::max<size_t>(1, static_cast<size_t>(p->n_fitems) * static_cast<size_t>(nwords(B)) * 64), s, cap,
+                   "check partials")) != GS_OK)
+        return st;
+    if ((st = grow(&p->stage, &p->stage_cap,
+                   std::max<size_t>(1, static_cast<size_t>(n_segments(p, B)) * std::max(p->h.n_inst, 1) * std::max(B, 1)),
+                   s, cap, "reduction stage")) != GS_OK)
+        return st;
     return GS_OK;
 }
 
@@ -457,6 +480,7 @@ gs_status check_batch(const gs_problem* p, int dtype, int32_t B, int64_t ldB) {
     const int vec = (dtype == kF32) ? 4 : 8;
     if (ldB % vec != 0)
         return fail(GS_ERR_INVALID_ARG, "ldB must be a multiple of 4 (float) / 8 (16-bit) elements");
+    if (ldB > (int64_t(1) << 30)) return fail(GS_ERR_INVALID_ARG, "ldB beyond 2^30 elements");
     if (p->h.n > 0 && ldB > (int64_t(1) << 40) / p->h.n) return fail(GS_ERR_INVALID_ARG, "ldB too large");
     return GS_OK;
 }
@@ -512,6 +536,8 @@ gs_status load(int32_t n_inst, const int64_t* n_vars, const int64_t* n_clauses, 
         delete p;
         return cuda_fail(e, "cudaGetDevice");
     }
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device) == cudaSuccess && sms > 0) p->sms = sms;
     HostPlan& H = p->h;
     p->n_fitems = static_cast<int32_t>(H.fitems.size());
     p->n_vitems = static_cast<int32_t>(H.vitems.size());
@@ -586,18 +612,53 @@ gs_status launch_check_all(gs_problem* p, const uint64_t* bits, int32_t B, int32
     cp.codes = p->fcodes;
     cp.ctab = p->fctab;
     cp.bits = bits;
-    cp.unsat = unsat;
+    cp.part16 = p->part16;
+    cp.bpad16 = nwd * 64;
     cp.head = p->ctl + 2;
     cp.status = p->status;
-    GS_CUDA(cudaMemsetAsync(unsat, 0, sizeof(int32_t) * static_cast<size_t>(p->h.n_inst) * B, s), "memset unsat");
     GS_CUDA(cudaMemsetAsync(p->ctl + 2, 0, sizeof(int32_t), s), "memset head");
     const int64_t total = static_cast<int64_t>(cp.n_items) * cp.n_wchunks;
     if (total > 0 && B > 0) {
         const int grid = static_cast<int>(std::min<int64_t>(grid_check(lw), total));
         GS_CUDA(launch_check(cp, lw, grid, s), "check kernel launch");
     }
-    GS_CUDA(launch_finalize_check(unsat, p->inst_empty, p->h.n_inst, B, best, s), "finalize launch");
+    GS_CUDA(launch_count_reduce(p->part16, nwd * 64, p->f_iptr, p->f_list, p->inst_empty, p->h.n_inst, B,
+                                n_segments(p, B), reinterpret_cast<int32_t*>(p->stage), unsat, best, s),
+            "count reduce launch");
     return GS_OK;
+}
+
+// cuTensorMapEncodeTiled from the driver, looked up once through the runtime.
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q{};
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
+    });
+    return fn;
+}
+
+// Tensor map of the relaxed values x as a 2-D tensor [n rows][B columns] (row stride ldB),
+// box = one row of 512 bytes (a full candidate chunk), for tile::gather4 copies.
+bool encode_rows_map(CUtensorMap* tm, const void* x, int dtype, int64_t n, int32_t B, int64_t ldB) {
+    PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+    if (!enc || n <= 0 || n > 0x7fffffffLL) return false;
+    const size_t es = (dtype == kF32) ? 4 : 2;
+    const CUtensorMapDataType dt = (dtype == kF32)    ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                   : (dtype == kBF16) ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
+                                                      : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
+    const cuuint64_t dims[2] = {static_cast<cuuint64_t>(B), static_cast<cuuint64_t>(n)};
+    const cuuint64_t strides[1] = {static_cast<cuuint64_t>(ldB) * es};
+    const cuuint32_t box[2] = {static_cast<cuuint32_t>(kRowBytes / es), 1u};
+    const cuuint32_t estr[2] = {1u, 1u};
+    return enc(tm, dt, 2, const_cast<void*>(x), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+               CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 gs_status var_pass(gs_problem* p, int mode, const void* x_in, int dtype, int32_t B, int64_t ldB, const double* dloss,
@@ -635,11 +696,18 @@ gs_status var_pass(gs_problem* p, int mode, const void* x_in, int dtype, int32_t
             "memset counters");
     const int64_t total = static_cast<int64_t>(vp.n_items) * c.n_chunks;
     if (total > 0) {
-        const int grid = static_cast<int>(std::min<int64_t>(grid_var_pass(dtype, mode, c.lc), total));
-        GS_CUDA(launch_var_pass(vp, dtype, mode, c.lc, grid, s), "variable pass launch");
+        alignas(64) CUtensorMap tm;
+        if (c.lc == 32 && p->var_gather == 2 && encode_rows_map(&tm, x_in, dtype, p->h.n, B, ldB)) {
+            const int grid = static_cast<int>(std::min<int64_t>(grid_var_ring(dtype, mode), total));
+            GS_CUDA(launch_var_ring(vp, &tm, dtype, mode, grid, s), "variable pass (TMA gather) launch");
+        } else {
+            const int grid = static_cast<int>(std::min<int64_t>(grid_var_pass(dtype, mode, c.lc), total));
+            GS_CUDA(launch_var_pass(vp, dtype, mode, c.lc, grid, s), "variable pass launch");
+        }
     }
     if (loss)
-        GS_CUDA(launch_loss_reduce(p->part, c.bpad, p->v_iptr, p->v_list, p->inst_empty, p->h.n_inst, B, loss, s),
+        GS_CUDA(launch_loss_reduce2(p->part, c.bpad, p->v_iptr, p->v_list, p->inst_empty, p->h.n_inst, B,
+                                    n_segments(p, B), p->stage, loss, s),
                 "loss reduce launch");
     return GS_OK;
 }
@@ -773,8 +841,10 @@ gs_status gs_set_tuning(gs_problem* p, const gs_tuning* t) {
     auto ok = [](int32_t l) { return l == 0 || l == 4 || l == 8 || l == 16 || l == 32; };
     if (!ok(t->var_lanes) || !ok(t->fwd_lanes))
         return fail(GS_ERR_INVALID_ARG, "lanes per candidate chunk must be 0, 4, 8, 16 or 32");
+    if (t->var_gather < 0 || t->var_gather > 2) return fail(GS_ERR_INVALID_ARG, "var_gather must be 0, 1 or 2");
     p->var_lc_max = t->var_lanes ? t->var_lanes : 32;
     p->fwd_lc_max = t->fwd_lanes ? t->fwd_lanes : 32;
+    p->var_gather = t->var_gather;
     return GS_OK;
 }
 
@@ -782,6 +852,7 @@ gs_status gs_get_tuning(const gs_problem* p, gs_tuning* t) {
     if (!p || !t) return fail(GS_ERR_INVALID_ARG, "null argument");
     t->var_lanes = p->var_lc_max;
     t->fwd_lanes = p->fwd_lc_max;
+    t->var_gather = p->var_gather;
     return GS_OK;
 }
 
@@ -798,6 +869,9 @@ gs_status gs_reserve(gs_problem* p, int32_t B, gs_dtype dtype) {
     const Chunking cf = chunking_for(dtype, B, p->fwd_lc_max);
     grid_var_pass(dtype, kModeGrad, cv.lc);
     grid_var_pass(dtype, kModeAdam, cv.lc);
+    grid_var_ring(dtype, kModeGrad);
+    grid_var_ring(dtype, kModeAdam);
+    tensor_map_encoder();
     grid_forward(dtype, cf.lc);
     grid_check(lanes_for_words(nwords(B)));
     GS_CUDA(cudaDeviceSynchronize(), "cudaDeviceSynchronize");
@@ -850,7 +924,8 @@ gs_status gs_forward(gs_problem* p, const void* x, gs_dtype dtype, int32_t B, in
         const int grid = static_cast<int>(std::min<int64_t>(grid_forward(dtype, c.lc), total));
         GS_CUDA(launch_forward(fp, dtype, c.lc, grid, s), "forward launch");
     }
-    GS_CUDA(launch_loss_reduce(p->part, c.bpad, p->f_iptr, p->f_list, p->inst_empty, p->h.n_inst, B, loss, s),
+    GS_CUDA(launch_loss_reduce2(p->part, c.bpad, p->f_iptr, p->f_list, p->inst_empty, p->h.n_inst, B,
+                                n_segments(p, B), p->stage, loss, s),
             "loss reduce launch");
     return GS_OK;
 }
@@ -970,8 +1045,9 @@ void gs_free(gs_problem* p) {
     if (!p) return;
     int dev = -1;
     if (cudaGetDevice(&dev) == cudaSuccess && dev == p->device) cudaDeviceSynchronize();
-    void* ptrs[] = {p->fcodes, p->fctab,  p->fitems,     p->vcodes, p->vrecs, p->vtab, p->vitems, p->f_iptr, p->f_list,
-                    p->v_iptr, p->v_list, p->inst_empty, p->status, p->ctl,   p->part, p->split,  p->bits};
+    void* ptrs[] = {p->fcodes, p->fctab,  p->fitems,     p->vcodes, p->vrecs, p->vtab,  p->vitems,
+                    p->f_iptr, p->f_list, p->v_iptr,     p->v_list, p->inst_empty, p->status, p->ctl,
+                    p->part,   p->split,  p->bits,       p->part16, p->stage};
     for (void* q : ptrs)
         if (q) cudaFree(q);
     delete p;

@@ -37,6 +37,15 @@ constexpr int kVarWarpBytes = 2 * kVarBufBytes + 16;
 constexpr int kWarps = 8;          // warps per CTA of the tiled kernels
 constexpr int kThreads = kWarps * 32;
 
+// TMA-gather variant of the variable-major pass (chunks of 32 lanes, 512-byte rows): per warp a
+// ring of kRingSlots slots, each filled by one tile::gather4 copy of 4 rows.
+constexpr int kRingWarps = 4;
+constexpr int kRingSlots = 6;
+constexpr int kRowBytes = 512;
+constexpr int kSlotBytes = 4 * kRowBytes;
+constexpr int kRingWarpBytes =
+    ((kRingSlots * kSlotBytes + 2 * kVarBufBytes + 16 + kRingSlots * 8) + 127) / 128 * 128;
+
 // ---------------------------------------------------------------------------------------------
 // Clause-major literal code (forward and check tiles), one uint32 per literal occurrence:
 //   bit 0     : negated literal
@@ -158,7 +167,8 @@ struct CheckParams {
     const uint32_t* codes;
     const uint16_t* ctab;
     const uint64_t* bits;    // [n][nwd]
-    int32_t* unsat;          // [n_inst][B], accumulated with integer atomics
+    uint16_t* part16;        // [n_items][bpad16] per-tile unsat counts
+    int32_t bpad16;          // nwd * 64
     int32_t* head;
     int32_t* status;
 };
@@ -169,11 +179,22 @@ constexpr int32_t kStatusTimeout = 1;
 // ---------------------------------------------------------------------------------------------
 // Launchers (gs_kernels.cu). They return cudaGetLastError() of the launch.
 cudaError_t launch_var_pass(const VarParams& p, int dtype, int mode, int lc, int grid, cudaStream_t s);
+// tmap: a CUtensorMap (128 bytes) over x_in as a 2-D tensor [n rows][B columns], box {32*VEC, 1}.
+cudaError_t launch_var_ring(const VarParams& p, const void* tmap, int dtype, int mode, int grid, cudaStream_t s);
+int grid_var_ring(int dtype, int mode);
 cudaError_t launch_forward(const FwdParams& p, int dtype, int lc, int grid, cudaStream_t s);
 cudaError_t launch_check(const CheckParams& p, int lw, int grid, cudaStream_t s);
 cudaError_t launch_loss_reduce(const float* part, int32_t bpad, const int32_t* inst_items_ptr,
                                const int32_t* inst_items, const int64_t* n_empty, int32_t n_inst,
                                int32_t B, double* loss, cudaStream_t s);
+// Two-stage fixed-order reductions over the tiles of each instance (n_seg segments in stage 1;
+// stage holds n_seg * n_inst * B values).
+cudaError_t launch_loss_reduce2(const float* part, int32_t bpad, const int32_t* iptr, const int32_t* items,
+                                const int64_t* n_empty, int32_t n_inst, int32_t B, int32_t n_seg, double* stage,
+                                double* loss, cudaStream_t s);
+cudaError_t launch_count_reduce(const uint16_t* part16, int32_t bpad16, const int32_t* iptr, const int32_t* items,
+                                const int64_t* n_empty, int32_t n_inst, int32_t B, int32_t n_seg, int32_t* stage,
+                                int32_t* unsat, int32_t* best, cudaStream_t s);
 cudaError_t launch_finalize_check(int32_t* unsat, const int64_t* n_empty, int32_t n_inst, int32_t B,
                                   int32_t* best, cudaStream_t s);
 cudaError_t launch_relax(const float* delta, void* x, int dtype, int64_t n, int32_t B, int64_t ldB,

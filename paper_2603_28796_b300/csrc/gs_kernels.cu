@@ -12,6 +12,7 @@
 // No floating-point atomics: gradients are gathered per variable over the occurrence lists,
 // split variables are combined in a fixed order by the last part to finish (integer counter),
 // and loss partials are summed per tile in FP32 (Kahan) and across tiles in FP64 in tile order.
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -66,15 +67,19 @@ __device__ __forceinline__ uint64_t global_ns() {
     return t;
 }
 // Wait for a phase of the mbarrier with a time limit (and an iteration limit, in case the
-// timer does not advance). Returns false on timeout.
-__device__ __noinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, uint64_t limit_ns) {
-    if (mbar_try_wait(bar, parity)) return true;
+// timer does not advance). Returns false on timeout. The first probe is inline; the bounded
+// polling loop is out of line.
+__device__ __noinline__ bool mbar_wait_slow(uint64_t* bar, uint32_t parity, uint64_t limit_ns) {
     const uint64_t t0 = global_ns();
     for (uint32_t it = 0; it < (1u << 26); ++it) {
         if (mbar_try_wait(bar, parity)) return true;
         if ((it & 255u) == 0u && global_ns() - t0 > limit_ns) return false;
     }
     return false;
+}
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, uint64_t limit_ns) {
+    if (mbar_try_wait(bar, parity)) return true;
+    return mbar_wait_slow(bar, parity, limit_ns);
 }
 
 struct Span {
@@ -321,24 +326,43 @@ __device__ __forceinline__ float2 dup2(float a) { return make_float2(a, a); }
 
 __device__ __forceinline__ void code_ab(uint32_t c, float& a, float& b) {
     const bool sent = (c >> kVShift) == kVSentinel;
-    a = sent ? 0.0f : ((c & kVNeg) ? 1.0f : -1.0f);
-    b = sent ? 1.0f : ((c & kVNeg) ? 0.0f : 1.0f);
+    a = sent ? 0.0f : __uint_as_float(0xbf800000u ^ ((c & kVNeg) << 31));
+    b = sent ? 1.0f : fmaf(-0.5f, a, 0.5f);
 }
+// Sign of d(own factor)/dx on the last code of an occurrence: +1 negated own literal, -1 positive.
+__device__ __forceinline__ float occ_sign(uint32_t last) {
+    return __uint_as_float(0xbf800000u ^ ((last & kVSelfNeg) << 29));
+}
+
+// Per-lane view of the relaxed values: row u of this lane's candidates is at base + u * row_bytes.
+struct RowView {
+    const char* base;
+    uint32_t row_bytes;
+    bool ok;   // the lane holds at least one candidate < B
+};
+__device__ __forceinline__ uint4 load_row(const RowView& rv, uint32_t u) {
+    return ld_gather16(rv.base + static_cast<uint64_t>(u) * rv.row_bytes);
+}
+
+// Loss credits of one variable's occurrences: the clause value U_t = f_own * LOO is credited at
+// the clause's position-0 literal. f_own is the variable's own factor, so the credits are summed
+// separately for positive (Cp) and negated (Cn) own literals and multiplied by 1 - x resp. x once,
+// when the variable is done.
+template <int H>
+struct Credits {
+    float2 p[H], n[H];
+};
 
 // General slot loop over the occurrence codes [cs, ce) of the group, NB codes per batch; an
 // occurrence ends at a code carrying kVEnd. R is the running leave-one-out product (prefix then
 // suffix of the occurrence's clause), restarted after each end.
 template <typename T, int VEC, int NB, bool LOSS>
-__device__ __forceinline__ void var_slots(const uint32_t* cd, int cs, int ce, const T* xcol, int64_t ldB, bool ld_ok,
-                                          float (&gacc)[VEC], float (&Ls)[VEC], float (&Lc)[VEC],
-                                          const float (&xs)[VEC]) {
+__device__ __forceinline__ void var_slots(const uint32_t* cd, int cs, int ce, const RowView& rv, float2 (&G2)[VEC / 2],
+                                          Credits<VEC / 2>& cr) {
     constexpr int H = VEC / 2;
-    float2 R[H], G2[H];
+    float2 R[H];
 #pragma unroll
-    for (int h = 0; h < H; ++h) {
-        R[h] = dup2(1.0f);
-        G2[h] = make_float2(gacc[2 * h], gacc[2 * h + 1]);
-    }
+    for (int h = 0; h < H; ++h) R[h] = dup2(1.0f);
     for (int s = cs; s < ce; s += NB) {
         uint32_t cw[NB];
         uint4 raw[NB];
@@ -348,7 +372,7 @@ __device__ __forceinline__ void var_slots(const uint32_t* cd, int cs, int ce, co
         for (int j = 0; j < NB; ++j) {
             const uint32_t u = cw[j] >> kVShift;
             raw[j] = make_uint4(0u, 0u, 0u, 0u);
-            if (ld_ok && u != kVSentinel) raw[j] = ld_gather16(xcol + static_cast<int64_t>(u) * ldB);
+            if (rv.ok && u != kVSentinel) raw[j] = load_row(rv, u);
         }
 #pragma unroll
         for (int j = 0; j < NB; ++j) {
@@ -358,7 +382,7 @@ __device__ __forceinline__ void var_slots(const uint32_t* cd, int cs, int ce, co
             float a, b;
             code_ab(c, a, b);
             const bool end = (c & kVEnd) != 0u;
-            const float sg = end ? ((c & kVSelfNeg) ? 1.0f : -1.0f) : 0.0f;
+            const float sg = end ? occ_sign(c) : 0.0f;
             float2 rn[H];
 #pragma unroll
             for (int h = 0; h < H; ++h) {
@@ -366,20 +390,17 @@ __device__ __forceinline__ void var_slots(const uint32_t* cd, int cs, int ce, co
                 G2[h] = __ffma2_rn(dup2(sg), rn[h], G2[h]);
                 R[h] = end ? dup2(1.0f) : rn[h];
             }
-            if (LOSS && (c & kVCredit)) {
-                const bool sneg = (c & kVSelfNeg) != 0u;
+            if (LOSS) {
+                const uint32_t f = c & (kVEnd | kVCredit | kVSelfNeg);
+                const float wp = (f == (kVEnd | kVCredit)) ? 1.0f : 0.0f;
+                const float wn = (f == (kVEnd | kVCredit | kVSelfNeg)) ? 1.0f : 0.0f;
 #pragma unroll
                 for (int h = 0; h < H; ++h) {
-                    kahan_add(Ls[2 * h], Lc[2 * h], (sneg ? xs[2 * h] : 1.0f - xs[2 * h]) * rn[h].x);
-                    kahan_add(Ls[2 * h + 1], Lc[2 * h + 1], (sneg ? xs[2 * h + 1] : 1.0f - xs[2 * h + 1]) * rn[h].y);
+                    cr.p[h] = __ffma2_rn(dup2(wp), rn[h], cr.p[h]);
+                    cr.n[h] = __ffma2_rn(dup2(wn), rn[h], cr.n[h]);
                 }
             }
         }
-    }
-#pragma unroll
-    for (int h = 0; h < H; ++h) {
-        gacc[2 * h] = G2[h].x;
-        gacc[2 * h + 1] = G2[h].y;
     }
 }
 
@@ -392,16 +413,14 @@ __device__ __forceinline__ void fixed_ab(uint32_t c, float& a, float& b) {
     if constexpr (K == 1) {
         code_ab(c, a, b);   // unit-clause sentinels only occur in K = 1 tiles
     } else {
-        const uint32_t pos = ~c & 1u;                        // 1 for a positive literal
-        a = __uint_as_float(0x3f800000u | (pos << 31));    // -1 positive, +1 negated
-        b = __uint_as_float(pos * 0x3f800000u);            //  1 positive,  0 negated
+        a = __uint_as_float(0xbf800000u ^ ((c & kVNeg) << 31));   // -1 positive, +1 negated
+        b = fmaf(-0.5f, a, 0.5f);                                  //  1 positive,  0 negated
     }
 }
 
 template <typename T, int VEC, int K, int OB, bool LOSS, bool TAIL>
-__device__ __forceinline__ void occ_batch(const uint32_t* cd, int s, int ce, const T* xcol, int64_t ldB, bool ld_ok,
-                                          float2 (&G2)[VEC / 2], float (&Ls)[VEC], float (&Lc)[VEC],
-                                          const float (&xs)[VEC]) {
+__device__ __forceinline__ void occ_batch(const uint32_t* cd, int s, int ce, const RowView& rv, float2 (&G2)[VEC / 2],
+                                          Credits<VEC / 2>& cr) {
     constexpr int H = VEC / 2;
     constexpr int NS = OB * K;
     uint32_t cw[NS];
@@ -412,8 +431,8 @@ __device__ __forceinline__ void occ_batch(const uint32_t* cd, int s, int ce, con
     for (int j = 0; j < NS; ++j) {
         raw[j] = make_uint4(0u, 0u, 0u, 0u);
         const uint32_t u = cw[j] >> kVShift;
-        const bool load = ld_ok && ((K > 1 && !TAIL) || u != kVSentinel);
-        if (load) raw[j] = ld_gather16(xcol + static_cast<int64_t>(u) * ldB);
+        const bool load = rv.ok && ((K > 1 && !TAIL) || u != kVSentinel);
+        if (load) raw[j] = load_row(rv, u);
     }
 #pragma unroll
     for (int o = 0; o < OB; ++o) {
@@ -432,34 +451,46 @@ __device__ __forceinline__ void occ_batch(const uint32_t* cd, int s, int ce, con
         }
         const uint32_t last = cw[o * K + K - 1];
         const bool valid = !TAIL || (s + o * K) < ce;
-        const float sg = valid ? ((last & kVSelfNeg) ? 1.0f : -1.0f) : 0.0f;
+        const float sg = valid ? occ_sign(last) : 0.0f;
 #pragma unroll
         for (int h = 0; h < H; ++h) G2[h] = __ffma2_rn(dup2(sg), prod[h], G2[h]);
-        if (LOSS && valid && (last & kVCredit)) {
-            const bool sneg = (last & kVSelfNeg) != 0u;
+        if (LOSS) {
+            const uint32_t f = valid ? (last & (kVCredit | kVSelfNeg)) : 0u;
+            const float wp = (f == kVCredit) ? 1.0f : 0.0f;
+            const float wn = (f == (kVCredit | kVSelfNeg)) ? 1.0f : 0.0f;
 #pragma unroll
             for (int h = 0; h < H; ++h) {
-                kahan_add(Ls[2 * h], Lc[2 * h], (sneg ? xs[2 * h] : 1.0f - xs[2 * h]) * prod[h].x);
-                kahan_add(Ls[2 * h + 1], Lc[2 * h + 1], (sneg ? xs[2 * h + 1] : 1.0f - xs[2 * h + 1]) * prod[h].y);
+                cr.p[h] = __ffma2_rn(dup2(wp), prod[h], cr.p[h]);
+                cr.n[h] = __ffma2_rn(dup2(wn), prod[h], cr.n[h]);
             }
         }
     }
 }
 
 template <typename T, int VEC, int K, bool LOSS>
-__device__ __forceinline__ void var_occ_fixed(const uint32_t* cd, int cs, int ce, const T* xcol, int64_t ldB,
-                                              bool ld_ok, float (&gacc)[VEC], float (&Ls)[VEC], float (&Lc)[VEC],
-                                              const float (&xs)[VEC]) {
-    constexpr int H = VEC / 2;
+__device__ __forceinline__ void var_occ_fixed(const uint32_t* cd, int cs, int ce, const RowView& rv,
+                                              float2 (&G2)[VEC / 2], Credits<VEC / 2>& cr) {
     constexpr int OB = (K == 1) ? 8 : (K == 2 ? 4 : 3);
     constexpr int NS = OB * K;
+    int s = cs;
+    for (; s + NS <= ce; s += NS) occ_batch<T, VEC, K, OB, LOSS, false>(cd, s, ce, rv, G2, cr);
+    if (s < ce) occ_batch<T, VEC, K, OB, LOSS, true>(cd, s, ce, rv, G2, cr);
+}
+
+// Gradient and (with LOSS) loss credits of one variable's occurrence codes [cs, ce).
+template <typename T, int VEC, int NB, bool LOSS>
+__device__ __forceinline__ void var_gather(int kk, const uint32_t* cd, int cs, int ce, const RowView& rv,
+                                           float (&gacc)[VEC], Credits<VEC / 2>& cr) {
+    constexpr int H = VEC / 2;
     float2 G2[H];
 #pragma unroll
-    for (int h = 0; h < H; ++h) G2[h] = make_float2(gacc[2 * h], gacc[2 * h + 1]);
-    int s = cs;
-    for (; s + NS <= ce; s += NS)
-        occ_batch<T, VEC, K, OB, LOSS, false>(cd, s, ce, xcol, ldB, ld_ok, G2, Ls, Lc, xs);
-    if (s < ce) occ_batch<T, VEC, K, OB, LOSS, true>(cd, s, ce, xcol, ldB, ld_ok, G2, Ls, Lc, xs);
+    for (int h = 0; h < H; ++h) G2[h] = dup2(0.0f);
+    switch (kk) {
+        case 1: var_occ_fixed<T, VEC, 1, LOSS>(cd, cs, ce, rv, G2, cr); break;
+        case 2: var_occ_fixed<T, VEC, 2, LOSS>(cd, cs, ce, rv, G2, cr); break;
+        case 3: var_occ_fixed<T, VEC, 3, LOSS>(cd, cs, ce, rv, G2, cr); break;
+        default: var_slots<T, VEC, NB, LOSS>(cd, cs, ce, rv, G2, cr); break;
+    }
 #pragma unroll
     for (int h = 0; h < H; ++h) {
         gacc[2 * h] = G2[h].x;
@@ -467,15 +498,15 @@ __device__ __forceinline__ void var_occ_fixed(const uint32_t* cd, int cs, int ce
     }
 }
 
-template <typename T, int VEC, int NB, bool LOSS>
-__device__ __forceinline__ void var_gather(int kk, const uint32_t* cd, int cs, int ce, const T* xcol, int64_t ldB,
-                                           bool ld_ok, float (&gacc)[VEC], float (&Ls)[VEC], float (&Lc)[VEC],
-                                           const float (&xs)[VEC]) {
-    switch (kk) {
-        case 1: var_occ_fixed<T, VEC, 1, LOSS>(cd, cs, ce, xcol, ldB, ld_ok, gacc, Ls, Lc, xs); break;
-        case 2: var_occ_fixed<T, VEC, 2, LOSS>(cd, cs, ce, xcol, ldB, ld_ok, gacc, Ls, Lc, xs); break;
-        case 3: var_occ_fixed<T, VEC, 3, LOSS>(cd, cs, ce, xcol, ldB, ld_ok, gacc, Ls, Lc, xs); break;
-        default: var_slots<T, VEC, NB, LOSS>(cd, cs, ce, xcol, ldB, ld_ok, gacc, Ls, Lc, xs); break;
+// Adds a variable's credited clause values, (1 - x) * Cp + x * Cn per candidate, to the tile's
+// compensated loss accumulator.
+template <int VEC>
+__device__ __forceinline__ void credit_flush(const Credits<VEC / 2>& cr, const float (&xs)[VEC], float (&Ls)[VEC],
+                                             float (&Lc)[VEC]) {
+#pragma unroll
+    for (int h = 0; h < VEC / 2; ++h) {
+        kahan_add(Ls[2 * h], Lc[2 * h], fmaf(1.0f - xs[2 * h], cr.p[h].x, xs[2 * h] * cr.n[h].x));
+        kahan_add(Ls[2 * h + 1], Lc[2 * h + 1], fmaf(1.0f - xs[2 * h + 1], cr.p[h].y, xs[2 * h + 1] * cr.n[h].y));
     }
 }
 
@@ -623,8 +654,12 @@ __device__ __forceinline__ void process_var_item(const VarParams& P, int w, cons
     const int cand0 = chunk * C::BC;
     const int lane_base = cand0 + li * VEC;
     const bool ld_ok = lane_base < P.B;
-    const T* xcol = static_cast<const T*>(P.x_in) + lane_base;
+    RowView rv;
+    rv.base = reinterpret_cast<const char*>(static_cast<const T*>(P.x_in) + lane_base);
+    rv.row_bytes = static_cast<uint32_t>(P.ldB * sizeof(T));
+    rv.ok = ld_ok;
     const bool loss = P.loss_part != nullptr;
+    constexpr int H = VEC / 2;
 
     float Ls[VEC], Lc[VEC];
 #pragma unroll
@@ -644,19 +679,22 @@ __device__ __forceinline__ void process_var_item(const VarParams& P, int w, cons
                 cs = rc[oa + (O * g) / G];
                 ce = rc[oa + (O * (g + 1)) / G];
             }
-            float xs[VEC];
-#pragma unroll
-            for (int e = 0; e < VEC; ++e) xs[e] = 0.0f;
-            if (loss && ld_ok) unpack<T>(ld_gather16(xcol + static_cast<int64_t>(v) * P.ldB), xs);
             AdamState<VPG> st;
             if constexpr (MODE == kModeAdam && C::PREFETCH) adam_prefetch<T, MODE, LC>(P, v, chunk, g, li, st);
             float gacc[VEC];
+            Credits<H> cr;
 #pragma unroll
-            for (int e = 0; e < VEC; ++e) gacc[e] = 0.0f;
-            if (loss)
-                var_gather<T, VEC, C::NB, true>(it.kk, cd, cs, ce, xcol, P.ldB, ld_ok, gacc, Ls, Lc, xs);
-            else
-                var_gather<T, VEC, C::NB, false>(it.kk, cd, cs, ce, xcol, P.ldB, ld_ok, gacc, Ls, Lc, xs);
+            for (int h = 0; h < H; ++h) cr.p[h] = cr.n[h] = dup2(0.0f);
+            if (loss) {
+                var_gather<T, VEC, C::NB, true>(it.kk, cd, cs, ce, rv, gacc, cr);
+                float xs[VEC];
+#pragma unroll
+                for (int e = 0; e < VEC; ++e) xs[e] = 0.0f;
+                if (ld_ok) unpack<T>(load_row(rv, static_cast<uint32_t>(v)), xs);
+                credit_flush<VEC>(cr, xs, Ls, Lc);
+            } else {
+                var_gather<T, VEC, C::NB, false>(it.kk, cd, cs, ce, rv, gacc, cr);
+            }
             group_sum<LC>(gacc);
             float ge[VPG];
 #pragma unroll
@@ -680,17 +718,20 @@ __device__ __forceinline__ void process_var_item(const VarParams& P, int w, cons
             cs = rc[(O * g) / G];
             ce = rc[(O * (g + 1)) / G];
         }
-        float xs[VEC];
-#pragma unroll
-        for (int e = 0; e < VEC; ++e) xs[e] = 0.0f;
-        if (loss && ld_ok) unpack<T>(ld_gather16(xcol + static_cast<int64_t>(v) * P.ldB), xs);
         float gacc[VEC];
+        Credits<H> cr;
 #pragma unroll
-        for (int e = 0; e < VEC; ++e) gacc[e] = 0.0f;
-        if (loss)
-            var_gather<T, VEC, C::NB, true>(it.kk, cd, cs, ce, xcol, P.ldB, ld_ok, gacc, Ls, Lc, xs);
-        else
-            var_gather<T, VEC, C::NB, false>(it.kk, cd, cs, ce, xcol, P.ldB, ld_ok, gacc, Ls, Lc, xs);
+        for (int h = 0; h < H; ++h) cr.p[h] = cr.n[h] = dup2(0.0f);
+        if (loss) {
+            var_gather<T, VEC, C::NB, true>(it.kk, cd, cs, ce, rv, gacc, cr);
+            float xs[VEC];
+#pragma unroll
+            for (int e = 0; e < VEC; ++e) xs[e] = 0.0f;
+            if (ld_ok) unpack<T>(load_row(rv, static_cast<uint32_t>(v)), xs);
+            credit_flush<VEC>(cr, xs, Ls, Lc);
+        } else {
+            var_gather<T, VEC, C::NB, false>(it.kk, cd, cs, ce, rv, gacc, cr);
+        }
         group_sum<LC>(gacc);
         float* rowp = P.split_part + static_cast<int64_t>(it.split_row + it.part) * P.bpad + lane_base;
         if (g == 0) {
@@ -773,6 +814,240 @@ __global__ void __launch_bounds__(kThreads, Elem<T>::VEC == 4 ? 3 : 2) k_var_pas
         }
         phase[buf] ^= 1u;
         process_var_item<T, MODE, LC>(P, w, wbase + buf * kVarBufBytes, g, li, lane);
+        __syncwarp();
+        w = wn;
+        buf ^= 1;
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+// Variable-major pass with TMA gathers (chunks of 32 lanes). The relaxed-value rows named by a
+// tile's occurrence codes are fetched four at a time by cp.async.bulk.tensor ... tile::gather4
+// into a per-warp ring of shared-memory slots, each completing on its own mbarrier, so many rows
+// are in flight per warp without occupying registers; lanes read their 16-byte slice of each
+// row from shared memory. A slot is refilled with the group kRingSlots ahead as soon as its four
+// codes have been consumed.
+__device__ __forceinline__ void gather4(void* dst, const CUtensorMap* tm, int col, int r0, int r1, int r2, int r3,
+                                        uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cta.global.tile::gather4.mbarrier::complete_tx::bytes "
+        "[%0], [%1, {%2, %3, %4, %5, %6}], [%7];" ::"r"(smem_addr(dst)),
+        "l"(reinterpret_cast<uint64_t>(tm)), "r"(col), "r"(r0), "r"(r1), "r"(r2), "r"(r3), "r"(smem_addr(bar))
+        : "memory");
+}
+
+struct Ring {
+    unsigned char* slots;
+    uint64_t* bars;
+    uint32_t phase;   // bit k: parity of slot k's next completion
+    int pend_lo;      // after a failed wait: groups [pend_lo, pend_hi) still have copies in flight
+    int pend_hi;
+};
+
+// Issues group g (codes 4g .. 4g+3 of the staged tile) into slot g % kRingSlots (lane 0 only).
+__device__ __forceinline__ void ring_issue(Ring& r, const CUtensorMap* tm, const uint32_t* cd, int n_codes, int g,
+                                           int col, uint32_t bytes) {
+    int rows[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int ci = 4 * g + i;
+        const uint32_t u = (ci < n_codes) ? (cd[ci] >> kVShift) : kVSentinel;
+        rows[i] = (u == kVSentinel) ? 0 : static_cast<int>(u);
+    }
+    const int slot = g % kRingSlots;
+    fence_proxy_async();
+    mbar_expect_tx(&r.bars[slot], bytes);
+    gather4(r.slots + slot * kSlotBytes, tm, col, rows[0], rows[1], rows[2], rows[3], &r.bars[slot]);
+}
+
+template <typename T, int MODE>
+__device__ __forceinline__ bool process_var_ring(const VarParams& P, const CUtensorMap* tm, int w,
+                                                 const unsigned char* buf, Ring& ring, int lane) {
+    using C = VarCfg<T, MODE, 32>;
+    constexpr int VEC = C::VEC, H = VEC / 2, VPG = C::VPG;
+    const int item = w % P.n_items;
+    const int chunk = w / P.n_items;
+    const VarItem it = P.items[item];
+    const uint32_t* vt =
+        reinterpret_cast<const uint32_t*>(buf + (reinterpret_cast<uintptr_t>(P.vtab + it.vtab_base) & 15));
+    const uint32_t* cd = reinterpret_cast<const uint32_t*>(
+        buf + kVarVtabBytes + kVarRecBytes + (reinterpret_cast<uintptr_t>(P.codes + it.code_base) & 15));
+    const int cand0 = chunk * C::BC;
+    const int lane_base = cand0 + lane * VEC;
+    const bool ld_ok = lane_base < P.B;
+    const T* xcol = static_cast<const T*>(P.x_in) + lane_base;
+    const bool loss = P.loss_part != nullptr;
+    const int n_codes = it.n_codes;
+    const int n_groups = (n_codes + 3) >> 2;
+    const uint32_t bytes = 4u * kRowBytes;
+
+    int issued = 0;
+    if (lane == 0)
+        for (int g = 0; g < n_groups && g < kRingSlots; ++g) ring_issue(ring, tm, cd, n_codes, g, cand0, bytes);
+    issued = n_groups < kRingSlots ? n_groups : kRingSlots;
+
+    float Ls[VEC], Lc[VEC];
+#pragma unroll
+    for (int e = 0; e < VEC; ++e) Ls[e] = Lc[e] = 0.0f;
+    int c = 0;
+    const int nv = (it.split < 0) ? it.nv : 1;
+    bool ok = true;
+    for (int vi = 0; vi < nv; ++vi) {
+        const int v = it.v0 + vi;
+        const int ce = (it.split < 0) ? static_cast<int>(vt[vi + 1] & 0xffffu) : n_codes;
+        float xs[VEC];
+#pragma unroll
+        for (int e = 0; e < VEC; ++e) xs[e] = 0.0f;
+        if (loss && ld_ok) unpack<T>(ld_gather16(xcol + static_cast<int64_t>(v) * P.ldB), xs);
+        AdamState<VPG> st;
+        if constexpr (MODE == kModeAdam)
+            if (it.split < 0) adam_prefetch<T, MODE, 32>(P, v, chunk, 0, lane, st);
+        float2 R[H], G2[H];
+#pragma unroll
+        for (int h = 0; h < H; ++h) {
+            R[h] = dup2(1.0f);
+            G2[h] = dup2(0.0f);
+        }
+        for (; c < ce; ++c) {
+            const int slot = (c >> 2) % kRingSlots;
+            if ((c & 3) == 0) {
+                const bool got = mbar_wait_bounded(&ring.bars[slot], (ring.phase >> slot) & 1u, kWaitNs);
+                if (!__all_sync(0xffffffffu, got)) {
+                    ring.pend_lo = c >> 2;
+                    ring.pend_hi = issued;
+                    ok = false;
+                    break;
+                }
+                ring.phase ^= 1u << slot;
+            }
+            const uint4 raw = *reinterpret_cast<const uint4*>(ring.slots + slot * kSlotBytes + (c & 3) * kRowBytes +
+                                                              lane * 16);
+            float xv[VEC];
+            unpack<T>(raw, xv);
+            const uint32_t code = cd[c];
+            float a, b;
+            code_ab(code, a, b);
+            const bool end = (code & kVEnd) != 0u;
+            const float sg = end ? ((code & kVSelfNeg) ? 1.0f : -1.0f) : 0.0f;
+            float2 rn[H];
+#pragma unroll
+            for (int h = 0; h < H; ++h) {
+                rn[h] = __fmul2_rn(R[h], __ffma2_rn(dup2(a), make_float2(xv[2 * h], xv[2 * h + 1]), dup2(b)));
+                G2[h] = __ffma2_rn(dup2(sg), rn[h], G2[h]);
+                R[h] = end ? dup2(1.0f) : rn[h];
+            }
+            if (loss && (code & kVCredit)) {
+                const bool sneg = (code & kVSelfNeg) != 0u;
+#pragma unroll
+                for (int h = 0; h < H; ++h) {
+                    kahan_add(Ls[2 * h], Lc[2 * h], (sneg ? xs[2 * h] : 1.0f - xs[2 * h]) * rn[h].x);
+                    kahan_add(Ls[2 * h + 1], Lc[2 * h + 1], (sneg ? xs[2 * h + 1] : 1.0f - xs[2 * h + 1]) * rn[h].y);
+                }
+            }
+            if ((c & 3) == 3) {   // group done: its slot takes the group kRingSlots ahead
+                __syncwarp();
+                if (lane == 0 && issued < n_groups) ring_issue(ring, tm, cd, n_codes, issued, cand0, bytes);
+                if (issued < n_groups) ++issued;
+            }
+        }
+        if (!ok) break;
+        float gacc[VEC];
+#pragma unroll
+        for (int h = 0; h < H; ++h) {
+            gacc[2 * h] = G2[h].x;
+            gacc[2 * h + 1] = G2[h].y;
+        }
+        if (it.split < 0) {
+            var_epilogue<T, MODE, 32>(P, v, it.inst, chunk, 0, lane, lane, gacc, st);
+        } else {
+            float* rowp = P.split_part + static_cast<int64_t>(it.split_row + it.part) * P.bpad + lane_base;
+#pragma unroll
+            for (int e = 0; e < VEC; e += 4)
+                __stcg(reinterpret_cast<float4*>(rowp + e), make_float4(gacc[e], gacc[e + 1], gacc[e + 2], gacc[e + 3]));
+            __threadfence();
+            __syncwarp();
+            int prev = 0;
+            if (lane == 0) prev = atomicAdd(&P.split_cnt[static_cast<int64_t>(it.split) * P.n_chunks + chunk], 1);
+            prev = __shfl_sync(0xffffffffu, prev, 0);
+            if (prev == it.n_parts - 1) {
+                __threadfence();
+                float ge[VPG];
+#pragma unroll
+                for (int el = 0; el < VPG; ++el) ge[el] = 0.0f;
+                const float* base = P.split_part + static_cast<int64_t>(it.split_row) * P.bpad + lane_base;
+                for (int q = 0; q < it.n_parts; ++q) {
+#pragma unroll
+                    for (int el = 0; el < VPG; ++el) ge[el] += __ldcg(base + static_cast<int64_t>(q) * P.bpad + el);
+                }
+                if constexpr (MODE == kModeAdam) adam_prefetch<T, MODE, 32>(P, v, chunk, 0, lane, st);
+                var_epilogue<T, MODE, 32>(P, v, it.inst, chunk, 0, lane, lane, ge, st);
+            }
+        }
+    }
+    if (!ok) return false;
+    if (loss) {
+        float* dst = P.loss_part + static_cast<int64_t>(item) * P.bpad + lane_base;
+#pragma unroll
+        for (int e = 0; e < VEC; e += 4)
+            __stcg(reinterpret_cast<float4*>(dst + e), make_float4(Ls[e] - Lc[e], Ls[e + 1] - Lc[e + 1],
+                                                                   Ls[e + 2] - Lc[e + 2], Ls[e + 3] - Lc[e + 3]));
+    }
+    return true;
+}
+
+template <typename T, int MODE>
+__global__ void __launch_bounds__(kRingWarps * 32) k_var_ring(const VarParams P, const __grid_constant__ CUtensorMap tm) {
+    extern __shared__ __align__(1024) unsigned char smem[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    unsigned char* wbase = smem + warp * kRingWarpBytes;
+    Ring ring;
+    ring.slots = wbase;
+    unsigned char* ibuf = wbase + kRingSlots * kSlotBytes;
+    uint64_t* ibars = reinterpret_cast<uint64_t*>(ibuf + 2 * kVarBufBytes);
+    ring.bars = ibars + 2;
+    ring.phase = 0u;
+    if (lane == 0) {
+        mbar_init(&ibars[0], 1);
+        mbar_init(&ibars[1], 1);
+        for (int k = 0; k < kRingSlots; ++k) mbar_init(&ring.bars[k], 1);
+        fence_mbar_init();
+    }
+    __syncwarp();
+    const int total = P.n_items * P.n_chunks;
+    int w = fetch_work(P.head, lane);
+    if (w < total && lane == 0) issue_var_item<T, MODE, 32>(P, w % P.n_items, ibuf, &ibars[0]);
+    uint32_t phase[2] = {0u, 0u};
+    int buf = 0;
+    while (w < total) {
+        const int wn = fetch_work(P.head, lane);
+        if (wn < total && lane == 0) {
+            fence_proxy_async();
+            issue_var_item<T, MODE, 32>(P, wn % P.n_items, ibuf + (buf ^ 1) * kVarBufBytes, &ibars[buf ^ 1]);
+        }
+        ring.pend_lo = ring.pend_hi = 0;
+        bool idx_ok = mbar_wait_bounded(&ibars[buf], phase[buf], kWaitNs);
+        idx_ok = __all_sync(0xffffffffu, idx_ok);
+        bool ok = idx_ok;
+        if (idx_ok) {
+            phase[buf] ^= 1u;
+            ok = process_var_ring<T, MODE>(P, &tm, w, ibuf + buf * kVarBufBytes, ring, lane);
+        }
+        if (!__all_sync(0xffffffffu, ok)) {
+            // a bounded wait gave up: record it, let this warp's copies in flight land (each wait
+            // bounded again), stop
+            if (lane == 0) {
+                atomicOr(P.status, kStatusTimeout);
+                if (!idx_ok) mbar_wait_bounded(&ibars[buf], phase[buf], kWaitNs);
+                if (wn < total) mbar_wait_bounded(&ibars[buf ^ 1], phase[buf ^ 1], kWaitNs);
+                for (int g = ring.pend_lo; g < ring.pend_hi; ++g) {
+                    const int k = g % kRingSlots;
+                    mbar_wait_bounded(&ring.bars[k], (ring.phase >> k) & 1u, kWaitNs);
+                    ring.phase ^= 1u << k;
+                }
+            }
+            __syncwarp();
+            return;
+        }
         __syncwarp();
         w = wn;
         buf ^= 1;
@@ -904,45 +1179,10 @@ __global__ void __launch_bounds__(kThreads) k_forward(const FwdParams P) {
 
 // ------------------------------------------------------------------------------------------
 // Exact check on bit-packed rounded assignments: per clause, sat = OR_i (literal true) over 64
-// candidates per word; unsat words are added into 64 bit-sliced counters per lane. The counters
-// persist across the tiles a warp processes and are flushed (one integer atomic per candidate
-// and lane group) when the instance or word chunk changes, before they could overflow, and at
-// the end of the kernel.
-constexpr int kPlanes = 16;                  // counts < 65536 per lane between flushes
-constexpr int kFlushAt = (1 << kPlanes) - 1 - kFwdClauses;
-
-template <int LW>
-__device__ __forceinline__ void check_flush(uint64_t (&planes)[kPlanes], int32_t* unsat, int inst, int B, int wd,
-                                            int nwd, int g) {
-#pragma unroll
-    for (int off = LW; off < 32; off <<= 1) {
-        uint64_t carry = 0ull;
-#pragma unroll
-        for (int p = 0; p < kPlanes; ++p) {
-            const uint64_t a = planes[p];
-            const uint64_t o = __shfl_xor_sync(0xffffffffu, a, off);
-            const uint64_t s = a ^ o ^ carry;
-            carry = (a & o) | (carry & (a ^ o));
-            planes[p] = s;
-        }
-    }
-    if (g == 0 && wd < nwd) {
-        int32_t* dst = unsat + static_cast<int64_t>(inst) * B + wd * 64;
-        uint64_t any = 0ull;
-#pragma unroll
-        for (int p = 0; p < kPlanes; ++p) any |= planes[p];
-        while (any) {
-            const int bit = __ffsll(static_cast<long long>(any)) - 1;
-            any &= any - 1ull;
-            int cnt = 0;
-#pragma unroll
-            for (int p = 0; p < kPlanes; ++p) cnt |= static_cast<int>((planes[p] >> bit) & 1ull) << p;
-            atomicAdd(dst + bit, cnt);
-        }
-    }
-#pragma unroll
-    for (int p = 0; p < kPlanes; ++p) planes[p] = 0ull;
-}
+// candidates per word; the unsat words of a tile are added into 64 bit-sliced counters per lane
+// (a tile has <= 256 clauses, so 9 planes), combined across lane groups, and written as one
+// uint16 count per (tile, candidate). A fixed-order reduction over tiles follows; no atomics.
+constexpr int kPlanes = 9;
 
 template <int LW>
 __global__ void __launch_bounds__(kThreads) k_check(const CheckParams P) {
@@ -959,10 +1199,6 @@ __global__ void __launch_bounds__(kThreads) k_check(const CheckParams P) {
         fence_mbar_init();
     }
     __syncwarp();
-    uint64_t planes[kPlanes];
-#pragma unroll
-    for (int p = 0; p < kPlanes; ++p) planes[p] = 0ull;
-    int cur_inst = -1, cur_wd = -1, pending = 0;
     const int total = P.n_items * P.n_wchunks;
     int w = fetch_work(P.head, lane);
     if (w < total && lane == 0) issue_fwd_item(P.items, P.codes, P.ctab, w % P.n_items, wbase, &bars[0]);
@@ -991,13 +1227,6 @@ __global__ void __launch_bounds__(kThreads) k_check(const CheckParams P) {
             const int wchunk = w / P.n_items;
             const FwdItem it = P.items[item];
             const int wd = wchunk * LW + li;
-            if (it.inst != cur_inst || wd != cur_wd || pending > kFlushAt) {
-                if (cur_inst >= 0) check_flush<LW>(planes, P.unsat, cur_inst, P.B, cur_wd, P.nwd, g);
-                cur_inst = it.inst;
-                cur_wd = wd;
-                pending = 0;
-            }
-            pending += it.n_clauses;
             const uint16_t* ct =
                 reinterpret_cast<const uint16_t*>(b + (reinterpret_cast<uintptr_t>(P.ctab + it.ctab_base) & 15));
             const uint32_t* cd = reinterpret_cast<const uint32_t*>(
@@ -1008,6 +1237,9 @@ __global__ void __launch_bounds__(kThreads) k_check(const CheckParams P) {
             const bool ok_w = wd < P.nwd;
             const int rem = P.B - wd * 64;
             const uint64_t vmask = (!ok_w || rem <= 0) ? 0ull : (rem >= 64 ? ~0ull : ((1ull << rem) - 1ull));
+            uint64_t planes[kPlanes];
+#pragma unroll
+            for (int p = 0; p < kPlanes; ++p) planes[p] = 0ull;
             uint64_t acc = 0ull;
             for (int s = cs; s < ce; s += NB) {
                 uint32_t cw[NB];
@@ -1027,7 +1259,8 @@ __global__ void __launch_bounds__(kThreads) k_check(const CheckParams P) {
                     if (c & kFEnd) {
                         uint64_t carry = ~acc & vmask;
                         acc = 0ull;
-                        for (int p = 0; p < kPlanes && carry; ++p) {
+#pragma unroll
+                        for (int p = 0; p < kPlanes; ++p) {
                             const uint64_t t = planes[p] & carry;
                             planes[p] ^= carry;
                             carry = t;
@@ -1035,12 +1268,108 @@ __global__ void __launch_bounds__(kThreads) k_check(const CheckParams P) {
                     }
                 }
             }
+#pragma unroll
+            for (int off = LW; off < 32; off <<= 1) {
+                uint64_t carry = 0ull;
+#pragma unroll
+                for (int p = 0; p < kPlanes; ++p) {
+                    const uint64_t a = planes[p];
+                    const uint64_t o = __shfl_xor_sync(0xffffffffu, a, off);
+                    const uint64_t sum = a ^ o ^ carry;
+                    carry = (a & o) | (carry & (a ^ o));
+                    planes[p] = sum;
+                }
+            }
+            if (g == 0 && ok_w) {
+                // 64 counts of this lane's word -> 32 uint32 pairs -> 8 vector stores
+                uint4* dst = reinterpret_cast<uint4*>(P.part16 + static_cast<int64_t>(item) * P.bpad16 + wd * 64);
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    uint32_t wv[4];
+#pragma unroll
+                    for (int r = 0; r < 4; ++r) {
+                        const int b0 = q * 8 + r * 2;
+                        uint32_t c0 = 0, c1 = 0;
+#pragma unroll
+                        for (int p = 0; p < kPlanes; ++p) {
+                            c0 |= static_cast<uint32_t>((planes[p] >> b0) & 1ull) << p;
+                            c1 |= static_cast<uint32_t>((planes[p] >> (b0 + 1)) & 1ull) << p;
+                        }
+                        wv[r] = c0 | (c1 << 16);
+                    }
+                    dst[q] = make_uint4(wv[0], wv[1], wv[2], wv[3]);
+                }
+            }
         }
         __syncwarp();
         w = wn;
         buf ^= 1;
     }
-    if (cur_inst >= 0) check_flush<LW>(planes, P.unsat, cur_inst, P.B, cur_wd, P.nwd, g);
+}
+
+// ------------------------------------------------------------------------------------------
+// Two-stage fixed-order reductions of per-tile partials over the tiles of each instance.
+// Stage 1: block (candidate slice of 32, instance, segment s) sums the segment's tiles (its 8
+// warps take tiles round-robin, then combine in warp order). Stage 2 sums the segments in order.
+template <typename PT, typename AT>
+__global__ void __launch_bounds__(256) k_reduce_tiles(const PT* part, int32_t stride, const int32_t* iptr,
+                                                      const int32_t* items, int32_t B, int32_t n_seg, AT* stage) {
+    __shared__ AT red[8][32];
+    const int inst = blockIdx.y, seg = blockIdx.z;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int b = blockIdx.x * 32 + lane;
+    const int a = iptr[inst], e = iptr[inst + 1];
+    const int len = e - a;
+    const int per = (len + n_seg - 1) / n_seg;
+    const int k0 = a + seg * per;
+    const int k1 = min(e, k0 + per);
+    AT s = AT(0);
+    if (b < B)
+        for (int k = k0 + warp; k < k1; k += 8) s += static_cast<AT>(part[static_cast<int64_t>(items[k]) * stride + b]);
+    red[warp][lane] = s;
+    __syncthreads();
+    if (warp == 0 && b < B) {
+        AT t = AT(0);
+#pragma unroll
+        for (int q = 0; q < 8; ++q) t += red[q][lane];
+        stage[(static_cast<int64_t>(seg) * gridDim.y + inst) * B + b] = t;
+    }
+}
+
+__global__ void __launch_bounds__(256) k_loss_final(const double* stage, int32_t n_seg, int32_t n_inst,
+                                                    const int64_t* n_empty, int32_t B, double* loss) {
+    const int inst = blockIdx.y;
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= B) return;
+    double t = 0.0;
+    for (int sgm = 0; sgm < n_seg; ++sgm) t += stage[(static_cast<int64_t>(sgm) * n_inst + inst) * B + b];
+    loss[static_cast<int64_t>(inst) * B + b] = t + static_cast<double>(n_empty[inst]);
+}
+
+// Per instance: unsat = sum of the segments + empty clauses (always unsatisfied); best = the
+// lowest candidate with the fewest unsatisfied clauses.
+__global__ void __launch_bounds__(1024) k_count_final(const int32_t* stage, int32_t n_seg, int32_t n_inst,
+                                                      const int64_t* n_empty, int32_t B, int32_t* unsat,
+                                                      int32_t* best) {
+    __shared__ unsigned long long red[1024];
+    const int inst = blockIdx.x;
+    const int32_t add = static_cast<int32_t>(n_empty[inst]);
+    unsigned long long key = ~0ull;
+    for (int b = threadIdx.x; b < B; b += blockDim.x) {
+        int32_t c = add;
+        for (int sgm = 0; sgm < n_seg; ++sgm) c += stage[(static_cast<int64_t>(sgm) * n_inst + inst) * B + b];
+        unsat[static_cast<int64_t>(inst) * B + b] = c;
+        const unsigned long long k = (static_cast<unsigned long long>(static_cast<uint32_t>(c)) << 32) |
+                                     static_cast<uint32_t>(b);
+        key = k < key ? k : key;
+    }
+    red[threadIdx.x] = key;
+    __syncthreads();
+    for (int st = blockDim.x / 2; st > 0; st >>= 1) {
+        if (threadIdx.x < st && red[threadIdx.x + st] < red[threadIdx.x]) red[threadIdx.x] = red[threadIdx.x + st];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0 && best) best[inst] = (B > 0) ? static_cast<int32_t>(red[0] & 0xffffffffull) : -1;
 }
 
 // ------------------------------------------------------------------------------------------
@@ -1180,6 +1509,22 @@ int var_grid_t() {
     if (!grid) grid = persistent_grid(k_var_pass<T, MODE, LC>, kWarps * kVarWarpBytes);
     return grid;
 }
+template <typename T, int MODE>
+int ring_grid_t() {
+    static int grid = 0;
+    if (!grid) {
+        const int smem = kRingWarps * kRingWarpBytes;
+        auto kernel = k_var_ring<T, MODE>;
+        cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+        int per_sm = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kRingWarps * 32, smem) != cudaSuccess ||
+            per_sm < 1)
+            per_sm = 1;
+        grid = per_sm * sm_count();
+    }
+    return grid;
+}
 template <typename T, int LC>
 int fwd_grid_t() {
     static int grid = 0;
@@ -1276,6 +1621,36 @@ cudaError_t launch_var_pass(const VarParams& p, int dtype, int mode, int lc, int
                              : var_launch_lc<__half, kModeGrad>(p, lc, grid, s);
 }
 
+int grid_var_ring(int dtype, int mode) {
+    if (dtype == kF32) return mode == kModeAdam ? ring_grid_t<float, kModeAdam>() : ring_grid_t<float, kModeGrad>();
+    if (dtype == kBF16)
+        return mode == kModeAdam ? ring_grid_t<__nv_bfloat16, kModeAdam>() : ring_grid_t<__nv_bfloat16, kModeGrad>();
+    return mode == kModeAdam ? ring_grid_t<__half, kModeAdam>() : ring_grid_t<__half, kModeGrad>();
+}
+
+cudaError_t launch_var_ring(const VarParams& p, const void* tmap, int dtype, int mode, int grid, cudaStream_t s) {
+    const int smem = kRingWarps * kRingWarpBytes;
+    const CUtensorMap& tm = *static_cast<const CUtensorMap*>(tmap);
+    grid_var_ring(dtype, mode);
+    if (dtype == kF32) {
+        if (mode == kModeAdam)
+            k_var_ring<float, kModeAdam><<<grid, kRingWarps * 32, smem, s>>>(p, tm);
+        else
+            k_var_ring<float, kModeGrad><<<grid, kRingWarps * 32, smem, s>>>(p, tm);
+    } else if (dtype == kBF16) {
+        if (mode == kModeAdam)
+            k_var_ring<__nv_bfloat16, kModeAdam><<<grid, kRingWarps * 32, smem, s>>>(p, tm);
+        else
+            k_var_ring<__nv_bfloat16, kModeGrad><<<grid, kRingWarps * 32, smem, s>>>(p, tm);
+    } else {
+        if (mode == kModeAdam)
+            k_var_ring<__half, kModeAdam><<<grid, kRingWarps * 32, smem, s>>>(p, tm);
+        else
+            k_var_ring<__half, kModeGrad><<<grid, kRingWarps * 32, smem, s>>>(p, tm);
+    }
+    return cudaGetLastError();
+}
+
 cudaError_t launch_forward(const FwdParams& p, int dtype, int lc, int grid, cudaStream_t s) {
     if (dtype == kF32) return fwd_launch_lc<float>(p, lc, grid, s);
     if (dtype == kBF16) return fwd_launch_lc<__nv_bfloat16>(p, lc, grid, s);
@@ -1301,6 +1676,27 @@ cudaError_t launch_loss_reduce(const float* part, int32_t bpad, const int32_t* i
     if (B <= 0 || n_inst <= 0) return cudaSuccess;
     dim3 grid((B + 31) / 32, n_inst);
     k_loss_reduce<<<grid, 256, 0, s>>>(part, bpad, inst_items_ptr, inst_items, n_empty, B, loss);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_loss_reduce2(const float* part, int32_t bpad, const int32_t* iptr, const int32_t* items,
+                                const int64_t* n_empty, int32_t n_inst, int32_t B, int32_t n_seg, double* stage,
+                                double* loss, cudaStream_t s) {
+    if (B <= 0 || n_inst <= 0) return cudaSuccess;
+    k_reduce_tiles<float, double><<<dim3((B + 31) / 32, n_inst, n_seg), 256, 0, s>>>(part, bpad, iptr, items, B,
+                                                                                      n_seg, stage);
+    k_loss_final<<<dim3((B + 255) / 256, n_inst), 256, 0, s>>>(stage, n_seg, n_inst, n_empty, B, loss);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_count_reduce(const uint16_t* part16, int32_t bpad16, const int32_t* iptr, const int32_t* items,
+                                const int64_t* n_empty, int32_t n_inst, int32_t B, int32_t n_seg, int32_t* stage,
+                                int32_t* unsat, int32_t* best, cudaStream_t s) {
+    if (n_inst <= 0) return cudaSuccess;
+    if (B > 0)
+        k_reduce_tiles<uint16_t, int32_t><<<dim3((B + 31) / 32, n_inst, n_seg), 256, 0, s>>>(part16, bpad16, iptr,
+                                                                                            items, B, n_seg, stage);
+    k_count_final<<<n_inst, 1024, 0, s>>>(stage, B > 0 ? n_seg : 0, n_inst, n_empty, B, unsat, best);
     return cudaGetLastError();
 }
 

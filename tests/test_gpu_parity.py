@@ -73,9 +73,11 @@ def test_forward_and_backward(name, B, dtype):
     H.assert_grad(H.host64(grad), g_ref, scale)
 
 
+@pytest.mark.parametrize("gather", [1, 2])
 @pytest.mark.parametrize("B", [33, 1024 + 40])
-def test_forward_backward_many_chunks(B):
+def test_forward_backward_many_chunks(B, gather):
     cnf, prob = get("3sat")
+    _abi.gs_set_tuning(prob, var_gather=gather)
     x = H.device_cands(synth.uniform_values(cnf.n_vars, B, seed=3), B, "f32")
     xh = H.host64(x)
     dl = torch.from_numpy(synth.normal_values(1, B, seed=4)[0].astype(np.float64)).cuda().reshape(1, B)
@@ -87,6 +89,7 @@ def test_forward_backward_many_chunks(B):
     w = dl.cpu().numpy()[0].astype(np.float32).astype(np.float64)
     H.assert_loss(loss.cpu().numpy()[0], lu)
     H.assert_grad(H.host64(grad), g_ref * w, scale * np.abs(w))
+    _abi.gs_set_tuning(prob)
 
 
 def test_boolean_points_exact():
@@ -106,11 +109,16 @@ def test_boolean_points_exact():
     assert np.array_equal(unsat.cpu().numpy()[0], lu.astype(np.int32))
 
 
+@pytest.mark.parametrize("gather", [1, 2])
 @pytest.mark.parametrize("dtype", ["f32", "bf16"])
 @pytest.mark.parametrize("B", [5, 64, 200])
 @pytest.mark.parametrize("name", ["3sat", "mixed", "edge", "community"])
-def test_fused_step(name, B, dtype):
+def test_fused_step(name, B, dtype, gather):
+    """gather 1: register loads, 2: TMA gather4 ring where a chunk spans 32 lanes (B = 200)."""
+    if gather == 2 and B != 200:
+        pytest.skip("register loads are the only path below 32 lanes per chunk")
     cnf, prob = get(name)
+    _abi.gs_set_tuning(prob, var_gather=gather)
     n = cnf.n_vars
     t = 3
     d0 = synth.init_delta(n, B, seed=11)
@@ -142,6 +150,7 @@ def test_fused_step(name, B, dtype):
     # where the oracle's delta' is clear of zero by more than the bound, the rounding agrees
     clear = np.abs(d_ref) > tol["delta"]
     assert np.array_equal(((dg > 0) == (d_ref > 0))[clear], np.ones(clear.sum(), bool))
+    _abi.gs_set_tuning(prob)
 
 
 @pytest.mark.parametrize("dtype", ["f32", "f16"])
