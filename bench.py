@@ -42,6 +42,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle sample")
+    ap.add_argument("--no-autotune", action="store_true", help="skip gs_autotune (use defaults / --var-* flags)")
     ap.add_argument("--var-lanes", type=int, default=0, help="cap on lanes per candidate chunk (gs_set_tuning)")
     ap.add_argument("--var-gather", type=int, default=0, help="0: automatic, 1: register loads, 2: TMA gather4 ring (gs_set_tuning)")
     return ap.parse_args()
@@ -209,6 +210,9 @@ def run_native(args):
     prob = _abi.gs_load_cnf(cnf.n_vars, cnf.clause_ptr, cnf.lits)
     if args.var_lanes or args.var_gather:
         _abi.gs_set_tuning(prob, var_lanes=args.var_lanes, var_gather=args.var_gather)
+    elif not args.no_autotune:
+        _abi.gs_autotune(prob, B, dtype)
+    tuning = _abi.gs_get_tuning(prob)
     info = prob.info()
     eng = Engine(prob, B, dtype, seed=1000 * rank + 1)
     nnz, n = cnf.nnz, cnf.n_vars
@@ -256,13 +260,13 @@ def run_native(args):
     value = evals_per_step * K * world / (total_ms / 1000.0)
     # roofline of the dominant kernel (fused variable-major pass inside gs_step)
     peak, peak_kind = measured_peaks()
-    lanes = args.var_lanes or 32
+    lanes = tuning["var_lanes"]
     n_chunks = -(-B // (lanes * (16 // s_bytes)))
     compulsory = n * B * (24 + 2 * s_bytes) + n * ((B + 63) // 64) * 8 + n_chunks * 4 * (
         info["n_occ_codes"] + info["n_var_tiles"] * 16)
     gather_model = nnz * B * 2 * s_bytes + n * B * (24 + s_bytes)
     mean_step_s = statistics.mean(step_ms) / 1000.0
-    achieved = compulsory / mean_step_s / 1e9
+    achieved = gather_model / mean_step_s / 1e9
     traffic = None
     try:
         with open(os.path.join(ROOT, "profiles", "var_pass_traffic.json")) as f:
@@ -273,11 +277,12 @@ def run_native(args):
         traffic = None
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": traffic, "peak_source": peak_kind,
-                "kernel": "k_var_pass (fused gradient+Adam+relax+round+loss credit), timed as the gs_step call",
-                "model": "compulsory bytes: n*B*(24+2s) state/value streams + bits + occurrence codes per chunk",
-                "bytes_per_launch": compulsory, "gather_model_bytes": gather_model,
-                "gather_model_GBps": gather_model / mean_step_s / 1e9,
-                "gather_model_frac": gather_model / mean_step_s / 1e9 / peak,
+                "kernel": "k_var_pass (fused gradient + Adam + relax + round + loss credit), timed as the gs_step call",
+                "model": "gather model: nnz*B*2s + n*B*(24+s) bytes per step (each literal value read once in "
+                         "forward and once in backward, state streamed once)",
+                "bytes_per_launch": gather_model,
+                "compulsory_bytes": compulsory, "compulsory_GBps": compulsory / mean_step_s / 1e9,
+                "compulsory_frac": compulsory / mean_step_s / 1e9 / peak,
                 "gs_step_ms": statistics.mean(step_ms), "check_ms": statistics.mean(check_ms)}
 
     cpu = None
@@ -323,8 +328,7 @@ def run_native(args):
                    "parallelism": "dp%d (independent candidate batches)" % world,
                    "l2": "inputs larger than L2: x %.0f MB + delta/m/v %.0f MB per step" % (
                        n * B * s_bytes / 1e6, n * B * 12 / 1e6),
-                   "steps_per_s": 1000.0 * K / total_ms, "var_lanes": args.var_lanes or 32,
-                   "var_gather": "tma_gather4" if args.var_gather == 2 else "registers"},
+                   "steps_per_s": 1000.0 * K / total_ms, "tuning": tuning},
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "gpu_launches": 4 * K,
     }
     if rank == 0:

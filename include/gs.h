@@ -169,6 +169,17 @@ gs_status gs_set_tuning(gs_problem* prob, const gs_tuning* tuning);
 gs_status gs_get_tuning(const gs_problem* prob, gs_tuning* tuning);
 
 /*
+ * gs_autotune - pick the tuning for batches of B candidates stored as dtype by timing the fused
+ * step (gs_step with grad = NULL and a loss) over the candidates-per-warp choices (lanes per
+ * chunk) and both gather modes, and gs_forward over its lanes per chunk, on temporary buffers
+ * it allocates and frees (n x B of each array). The fastest setting is applied to the problem
+ * (gs_set_tuning), written to *out when out is not NULL, and the workspace is reserved for it.
+ * Synchronous; not allowed during stream capture (GS_ERR_STATE). Errors: GS_ERR_INVALID_ARG,
+ * GS_ERR_OOM, GS_ERR_CUDA.
+ */
+gs_status gs_autotune(gs_problem* prob, int32_t B, gs_dtype dtype, gs_stream stream, gs_tuning* out);
+
+/*
  * gs_relax - relaxed values x = sigma(delta / tau) (Eq. 3 with two states and no Gumbel
  * noise), rounded to nearest-even when dtype is 16-bit.
  *   delta  device float [n][ldB] (input).   x  device dtype [n][ldB] (output).

@@ -27,7 +27,7 @@ STATUS_NAMES = {
 # Every symbol include/gs.h declares.
 EXPORTED = (
     "gs_adam_default", "gs_load_cnf", "gs_load_batch", "gs_load_dimacs", "gs_inspect_cnf", "gs_info_get",
-    "gs_set_tuning", "gs_get_tuning", "gs_reserve", "gs_relax", "gs_forward", "gs_forward_noalloc", "gs_backward", "gs_step", "gs_round_check", "gs_check_bits",
+    "gs_set_tuning", "gs_get_tuning", "gs_autotune", "gs_reserve", "gs_relax", "gs_forward", "gs_forward_noalloc", "gs_backward", "gs_step", "gs_round_check", "gs_check_bits",
     "gs_wait_selftest", "gs_sync_status", "gs_free", "gs_status_str", "gs_last_error",
 )
 
@@ -89,6 +89,7 @@ def lib():
             "gs_info_get": (ctypes.c_int, [vp, ctypes.POINTER(GsInfo)]),
             "gs_set_tuning": (ctypes.c_int, [vp, ctypes.POINTER(GsTuning)]),
             "gs_get_tuning": (ctypes.c_int, [vp, ctypes.POINTER(GsTuning)]),
+            "gs_autotune": (ctypes.c_int, [vp, i32, ctypes.c_int, vp, ctypes.POINTER(GsTuning)]),
             "gs_reserve": (ctypes.c_int, [vp, i32, ctypes.c_int]),
             "gs_relax": (ctypes.c_int, [vp, vp, vp, ctypes.c_int, i32, i64, ctypes.c_float, vp]),
             "gs_forward": (ctypes.c_int, [vp, vp, ctypes.c_int, i32, i64, vp, vp]),
@@ -263,6 +264,15 @@ def gs_set_tuning(prob: Problem, var_lanes: int = 0, fwd_lanes: int = 0, var_gat
 def gs_get_tuning(prob: Problem) -> dict:
     t = GsTuning()
     _check(lib().gs_get_tuning(prob.handle, ctypes.byref(t)), "gs_get_tuning")
+    return {"var_lanes": int(t.var_lanes), "fwd_lanes": int(t.fwd_lanes), "var_gather": int(t.var_gather)}
+
+
+def gs_autotune(prob: Problem, B: int, dtype, stream=None) -> dict:
+    code = dtype if isinstance(dtype, int) else {"f32": GS_F32, "bf16": GS_BF16, "f16": GS_F16}.get(dtype)
+    if code is None:
+        code = _dtype_code(_torch().empty(0, dtype=dtype))
+    t = GsTuning()
+    _check(lib().gs_autotune(prob.handle, int(B), code, _stream(stream), ctypes.byref(t)), "gs_autotune")
     return {"var_lanes": int(t.var_lanes), "fwd_lanes": int(t.fwd_lanes), "var_gather": int(t.var_gather)}
 
 

@@ -856,6 +856,108 @@ gs_status gs_get_tuning(const gs_problem* p, gs_tuning* t) {
     return GS_OK;
 }
 
+gs_status gs_autotune(gs_problem* p, int32_t B, gs_dtype dtype, gs_stream stream, gs_tuning* out) {
+    if (!p) return fail(GS_ERR_INVALID_ARG, "null problem");
+    gs_status st = check_device(p);
+    if (st != GS_OK) return st;
+    const int64_t ldB = ((static_cast<int64_t>(std::max(B, 1)) + 7) / 8) * 8;
+    if ((st = check_batch(p, dtype, B, ldB)) != GS_OK) return st;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (capturing(s)) return fail(GS_ERR_STATE, "gs_autotune cannot run during stream capture");
+    const int64_t n = p->h.n;
+    if (n == 0 || B == 0) {
+        if (out) gs_get_tuning(p, out);
+        return GS_OK;
+    }
+    // temporary candidate arrays: delta, m, v, grad (float) and two value buffers (dtype)
+    const size_t es = (static_cast<int>(dtype) == kF32) ? 4 : 2;
+    const size_t fbytes = static_cast<size_t>(n) * ldB * 4, xbytes = static_cast<size_t>(n) * ldB * es;
+    void* mem = nullptr;
+    if (cudaMalloc(&mem, 3 * fbytes + 2 * xbytes + static_cast<size_t>(B) * 8 + 256) != cudaSuccess)
+        return fail(GS_ERR_OOM, "gs_autotune temporaries");
+    char* base = static_cast<char*>(mem);
+    float* delta = reinterpret_cast<float*>(base);
+    float* m = reinterpret_cast<float*>(base + fbytes);
+    float* v = reinterpret_cast<float*>(base + 2 * fbytes);
+    void* x0 = base + 3 * fbytes;
+    void* x1 = base + 3 * fbytes + xbytes;
+    double* loss = reinterpret_cast<double*>(base + 3 * fbytes + 2 * xbytes);
+    auto cleanup = [&]() { cudaFree(mem); };
+    // deterministic contents: delta from zeroed memory relaxes to 1/2; a few steps move it
+    if (cudaMemsetAsync(mem, 0, 3 * fbytes, s) != cudaSuccess) {
+        cleanup();
+        return fail(GS_ERR_CUDA, "gs_autotune memset");
+    }
+    const gs_tuning saved{p->var_lc_max, p->fwd_lc_max, p->var_gather};
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    auto timed = [&](auto&& fn) -> float {
+        for (int i = 0; i < 2; ++i)
+            if (fn() != GS_OK) return -1.0f;
+        cudaEventRecord(e0, s);
+        for (int i = 0; i < 3; ++i)
+            if (fn() != GS_OK) return -1.0f;
+        cudaEventRecord(e1, s);
+        cudaEventSynchronize(e1);
+        float ms = 0.0f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        return ms / 3.0f;
+    };
+    int64_t step = 0;
+    gs_status rs = gs_relax(p, delta, x0, dtype, B, ldB, 1.0f, stream);
+    // variable-major pass: candidates per warp (lanes per chunk) x gather mode
+    gs_tuning best = saved;
+    float best_ms = -1.0f;
+    int tried = 0;   // bit lc: effective chunk width already timed
+    for (int lanes = 32; lanes >= 4 && rs == GS_OK; lanes /= 2) {
+        const int lc = chunking_for(dtype, B, lanes).lc;
+        if (tried & lc) continue;
+        tried |= lc;
+        for (int gather = 1; gather <= 2; ++gather) {
+            if (gather == 2 && lc != 32) continue;
+            p->var_lc_max = lanes;
+            p->var_gather = gather;
+            if ((rs = ensure_ws(p, dtype, B, false, s)) != GS_OK) break;
+            const float ms = timed([&] {
+                return gs_step(p, delta, m, v, nullptr, x0, x1, dtype, B, ldB, ++step, nullptr, loss, nullptr, stream);
+            });
+            if (ms > 0.0f && (best_ms < 0.0f || ms < best_ms)) {
+                best_ms = ms;
+                best.var_lanes = lanes;
+                best.var_gather = gather;
+            }
+        }
+    }
+    // clause-major forward: lanes per chunk
+    float best_f = -1.0f;
+    tried = 0;
+    for (int lanes = 32; lanes >= 4 && rs == GS_OK; lanes /= 2) {
+        const int lc = chunking_for(dtype, B, lanes).lc;
+        if (tried & lc) continue;
+        tried |= lc;
+        p->fwd_lc_max = lanes;
+        if ((rs = ensure_ws(p, dtype, B, false, s)) != GS_OK) break;
+        const float ms = timed([&] { return gs_forward(p, x0, dtype, B, ldB, loss, stream); });
+        if (ms > 0.0f && (best_f < 0.0f || ms < best_f)) {
+            best_f = ms;
+            best.fwd_lanes = lanes;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    const cudaError_t se = cudaStreamSynchronize(s);
+    cleanup();
+    p->var_lc_max = saved.var_lanes;
+    p->fwd_lc_max = saved.fwd_lanes;
+    p->var_gather = saved.var_gather;
+    if (rs != GS_OK) return rs;
+    if (se != cudaSuccess) return cuda_fail(se, "gs_autotune");
+    if ((st = gs_set_tuning(p, &best)) != GS_OK) return st;
+    if (out) *out = best;
+    return gs_reserve(p, B, dtype);
+}
+
 gs_status gs_reserve(gs_problem* p, int32_t B, gs_dtype dtype) {
     if (!p) return fail(GS_ERR_INVALID_ARG, "null problem");
     gs_status st = check_device(p);

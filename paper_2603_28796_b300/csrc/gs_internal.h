@@ -38,11 +38,13 @@ constexpr int kWarps = 8;          // warps per CTA of the tiled kernels
 constexpr int kThreads = kWarps * 32;
 
 // TMA-gather variant of the variable-major pass (chunks of 32 lanes, 512-byte rows): per warp a
-// ring of kRingSlots slots, each filled by one tile::gather4 copy of 4 rows.
-constexpr int kRingWarps = 4;
-constexpr int kRingSlots = 6;
+// ring of kRingSlots slots; a slot holds one batch of kRingBatch rows, fetched by
+// kRingBatch / 4 tile::gather4 copies completing on the slot's mbarrier.
+constexpr int kRingWarps = 2;
+constexpr int kRingSlots = 4;
+constexpr int kRingBatch = 8;
 constexpr int kRowBytes = 512;
-constexpr int kSlotBytes = 4 * kRowBytes;
+constexpr int kSlotBytes = kRingBatch * kRowBytes;
 constexpr int kRingWarpBytes =
     ((kRingSlots * kSlotBytes + 2 * kVarBufBytes + 16 + kRingSlots * 8) + 127) / 128 * 128;
 

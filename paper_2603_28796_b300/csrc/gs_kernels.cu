@@ -997,7 +997,7 @@ __device__ __forceinline__ bool process_var_ring(const VarParams& P, const CUten
 
 template <typename T, int MODE>
 __global__ void __launch_bounds__(kRingWarps * 32) k_var_ring(const VarParams P, const __grid_constant__ CUtensorMap tm) {
-    extern __shared__ __align__(1024) unsigned char smem[];
+    extern __shared__ __align__(128) unsigned char smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     unsigned char* wbase = smem + warp * kRingWarpBytes;
     Ring ring;
@@ -1420,15 +1420,26 @@ __global__ void __launch_bounds__(256) k_finalize_check(int32_t* unsat, const in
     if (threadIdx.x == 0 && best) best[inst] = (B > 0) ? static_cast<int32_t>(red[0] & 0xffffffffull) : -1;
 }
 
-// Relaxed values x = sigma(delta / tau), written as T.
+// Relaxed values x = sigma(delta / tau), written as T: one thread per 4 consecutive candidates of
+// a row (16-byte loads; the row stride keeps every group aligned), scalar tail past B.
 template <typename T>
 __global__ void __launch_bounds__(256) k_relax(const float* delta, T* x, int64_t n, int32_t B, int64_t ldB,
                                                float inv_tau) {
-    const int64_t total = n * B;
+    const int64_t groups = (B + 3) / 4;
+    const int64_t total = n * groups;
     for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < total;
          i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-        const int64_t v = i / B, b = i - v * B;
-        x[v * ldB + b] = from_f32<T>(sigmoid(delta[v * ldB + b] * inv_tau));
+        const int64_t v = i / groups, b = (i - v * groups) * 4;
+        const int64_t o = v * ldB + b;
+        if (b + 4 <= B) {
+            float d[4], y[4];
+            ld_stream<4>(delta + o, d);
+#pragma unroll
+            for (int e = 0; e < 4; ++e) y[e] = sigmoid(d[e] * inv_tau);
+            st_vals<T, 4>(x + o, y);
+        } else {
+            for (int64_t e = b; e < B; ++e) x[v * ldB + e] = from_f32<T>(sigmoid(delta[v * ldB + e] * inv_tau));
+        }
     }
 }
 
@@ -1710,7 +1721,7 @@ cudaError_t launch_finalize_check(int32_t* unsat, const int64_t* n_empty, int32_
 cudaError_t launch_relax(const float* delta, void* x, int dtype, int64_t n, int32_t B, int64_t ldB, float inv_tau,
                          cudaStream_t s) {
     if (n * B == 0) return cudaSuccess;
-    const int grid = elementwise_grid(n * B);
+    const int grid = elementwise_grid(n * ((B + 3) / 4));
     if (dtype == kF32)
         k_relax<float><<<grid, 256, 0, s>>>(delta, static_cast<float*>(x), n, B, ldB, inv_tau);
     else if (dtype == kBF16)

@@ -59,7 +59,7 @@ def gs_loss(prob: _abi.Problem, x: torch.Tensor) -> torch.Tensor:
 
 class Engine:
     def __init__(self, prob: _abi.Problem, B: int, dtype="f32", adam: Optional[dict] = None, seed: int = 0,
-                 delta0: Optional[np.ndarray] = None, device="cuda"):
+                 delta0: Optional[np.ndarray] = None, device="cuda", autotune: bool = False):
         self.prob = prob
         self.B = int(B)
         self.dtype = _DTYPES[dtype]
@@ -78,6 +78,8 @@ class Engine:
         self.best = torch.zeros(prob.n_inst, dtype=torch.int32, device=device)
         self.cur = 0
         self.t = 0
+        if autotune:
+            self.tuning = _abi.gs_autotune(prob, B, _CODES[self.dtype])
         _abi.gs_reserve(prob, B, _CODES[self.dtype])
         self.reset(seed, delta0)
 

@@ -313,3 +313,20 @@ def test_capture_without_reserve_is_refused():
         with torch.cuda.graph(g, stream=s):
             _abi.gs_forward(prob, x)
     assert ei.value.status == 7
+
+
+def test_autotune_picks_a_valid_tuning_and_keeps_results():
+    cnf, prob = get("3sat")
+    B = 200
+    t = _abi.gs_autotune(prob, B, "f32")
+    assert t["var_lanes"] in (4, 8, 16, 32) and t["fwd_lanes"] in (4, 8, 16, 32) and t["var_gather"] in (1, 2)
+    assert _abi.gs_get_tuning(prob) == t
+    x = H.device_cands(synth.uniform_values(cnf.n_vars, B, seed=9), B)
+    loss = _abi.gs_forward(prob, x)
+    grad = _abi.gs_backward(prob, x)
+    torch.cuda.synchronize()
+    lu, _ = oracle.forward(cnf.n_vars, cnf.clause_ptr, cnf.lits, H.host64(x))
+    g_ref, scale = oracle.backward(cnf.n_vars, cnf.clause_ptr, cnf.lits, H.host64(x))
+    H.assert_loss(loss.cpu().numpy()[0], lu)
+    H.assert_grad(H.host64(grad), g_ref, scale)
+    _abi.gs_set_tuning(prob)
