@@ -16,6 +16,7 @@
 
 #include "gs.h"
 #include "gs_internal.h"
+#include "gs_plan.h"
 
 using namespace gs;
 
@@ -37,295 +38,6 @@ gs_status cuda_fail(cudaError_t e, const char* what) {
         cudaError_t e__ = (call);                            \
         if (e__ != cudaSuccess) return cuda_fail(e__, what); \
     } while (0)
-
-// ---------------------------------------------------------------------------------------------
-// Host image of the device structures.
-struct HostPlan {
-    int64_t n = 0, m = 0, nnz = 0;
-    int32_t n_inst = 0, max_k = 0;
-    int64_t n_empty = 0, n_unit = 0, n_taut = 0, n_dup = 0;
-    std::vector<int64_t> var_off, clause_off, inst_empty;
-    // clause tiles
-    std::vector<uint32_t> fcodes;
-    std::vector<uint16_t> fctab;
-    std::vector<FwdItem> fitems;
-    // occurrence tiles
-    std::vector<uint32_t> vcodes;
-    std::vector<uint16_t> vrecs;
-    std::vector<uint32_t> vtab;
-    std::vector<VarItem> vitems;
-    int32_t n_split = 0, n_split_rows = 0;
-    // per-instance tile lists (ascending tile ids)
-    std::vector<int32_t> f_iptr, f_list, v_iptr, v_list;
-};
-
-// Validation + statistics. Fills plan.{n, m, nnz, n_inst, max_k, stats, var_off, clause_off,
-// inst_empty}.
-gs_status validate(int32_t n_inst, const int64_t* n_vars, const int64_t* n_clauses, const int64_t* clause_ptr,
-                   const int32_t* lits, HostPlan& P) {
-    if (n_inst < 1) return fail(GS_ERR_INVALID_ARG, "n_inst must be >= 1");
-    if (!n_vars || !n_clauses || !clause_ptr) return fail(GS_ERR_INVALID_ARG, "null n_vars/n_clauses/clause_ptr");
-    P.n_inst = n_inst;
-    P.var_off.assign(n_inst + 1, 0);
-    P.clause_off.assign(n_inst + 1, 0);
-    P.inst_empty.assign(n_inst, 0);
-    for (int32_t i = 0; i < n_inst; ++i) {
-        if (n_vars[i] < 0 || n_clauses[i] < 0) return fail(GS_ERR_INVALID_ARG, "negative n_vars or n_clauses");
-        P.var_off[i + 1] = P.var_off[i] + n_vars[i];
-        P.clause_off[i + 1] = P.clause_off[i] + n_clauses[i];
-        if (P.var_off[i + 1] > kMaxVars) return fail(GS_ERR_UNSUPPORTED, "too many variables (limit 2^28 - 2)");
-        if (P.clause_off[i + 1] > (int64_t(1) << 40)) return fail(GS_ERR_UNSUPPORTED, "too many clauses");
-    }
-    P.n = P.var_off[n_inst];
-    P.m = P.clause_off[n_inst];
-    if (clause_ptr[0] != 0) return fail(GS_ERR_INVALID_ARG, "clause_ptr[0] must be 0");
-    for (int64_t t = 0; t < P.m; ++t) {
-        const int64_t k = clause_ptr[t + 1] - clause_ptr[t];
-        if (k < 0) return fail(GS_ERR_INVALID_ARG, "clause_ptr is decreasing at clause " + std::to_string(t));
-        if (k > kMaxClauseWidth)
-            return fail(GS_ERR_UNSUPPORTED, "clause " + std::to_string(t) + " has " + std::to_string(k) +
-                                                " literals (limit 256)");
-    }
-    P.nnz = clause_ptr[P.m];
-    if (P.nnz > 0 && !lits) return fail(GS_ERR_INVALID_ARG, "null lits");
-    std::vector<int32_t> tmp;
-    for (int32_t i = 0; i < n_inst; ++i) {
-        const int64_t nv = n_vars[i];
-        for (int64_t t = P.clause_off[i]; t < P.clause_off[i + 1]; ++t) {
-            const int64_t a = clause_ptr[t], b = clause_ptr[t + 1];
-            const int k = static_cast<int>(b - a);
-            P.max_k = std::max(P.max_k, k);
-            if (k == 0) {
-                P.n_empty++;
-                P.inst_empty[i]++;
-            }
-            if (k == 1) P.n_unit++;
-            for (int64_t j = a; j < b; ++j) {
-                const int64_t l = lits[j];
-                const int64_t av = l < 0 ? -l : l;
-                if (l == 0 || av > nv)
-                    return fail(GS_ERR_INVALID_ARG, "literal " + std::to_string(l) + " of clause " + std::to_string(t) +
-                                                        " outside 1.." + std::to_string(nv));
-            }
-            tmp.assign(lits + a, lits + b);
-            std::sort(tmp.begin(), tmp.end(), [](int32_t x, int32_t y) {
-                const int32_t ax = x < 0 ? -x : x, ay = y < 0 ? -y : y;
-                return ax != ay ? ax < ay : x < y;
-            });
-            bool dup = false, taut = false;
-            for (int j = 1; j < k; ++j) {
-                if (tmp[j] == tmp[j - 1]) dup = true;
-                if (tmp[j] == -tmp[j - 1]) taut = true;
-            }
-            P.n_dup += dup;
-            P.n_taut += taut;
-        }
-    }
-    return GS_OK;
-}
-
-inline int64_t lit_row(const HostPlan& P, int32_t inst, int32_t lit) {
-    return P.var_off[inst] + (lit < 0 ? -static_cast<int64_t>(lit) : lit) - 1;
-}
-
-// Clause tiles: consecutive whole clauses of one instance, <= kFwdCodes codes, <= kFwdClauses.
-void build_fwd(const int64_t* clause_ptr, const int32_t* lits, HostPlan& P) {
-    P.fcodes.reserve(P.nnz);
-    P.f_iptr.assign(P.n_inst + 1, 0);
-    for (int32_t inst = 0; inst < P.n_inst; ++inst) {
-        int64_t t = P.clause_off[inst];
-        const int64_t te = P.clause_off[inst + 1];
-        while (t < te) {
-            FwdItem it{};
-            it.code_base = static_cast<int64_t>(P.fcodes.size());
-            it.ctab_base = static_cast<int64_t>(P.fctab.size());
-            it.inst = inst;
-            int nc = 0, ncodes = 0;
-            while (t < te && nc < kFwdClauses) {
-                const int k = static_cast<int>(clause_ptr[t + 1] - clause_ptr[t]);
-                if (ncodes + k > kFwdCodes) break;
-                P.fctab.push_back(static_cast<uint16_t>(ncodes));
-                for (int i = 0; i < k; ++i) {
-                    const int32_t l = lits[clause_ptr[t] + i];
-                    uint32_t c = static_cast<uint32_t>(lit_row(P, inst, l)) << kFShift;
-                    if (l < 0) c |= kFNeg;
-                    if (i == k - 1) c |= kFEnd;
-                    P.fcodes.push_back(c);
-                }
-                ncodes += k;
-                ++nc;
-                ++t;
-            }
-            P.fctab.push_back(static_cast<uint16_t>(ncodes));
-            it.n_codes = ncodes;
-            it.n_clauses = nc;
-            P.fitems.push_back(it);
-        }
-        P.f_iptr[inst + 1] = static_cast<int32_t>(P.fitems.size());
-    }
-    P.f_list.resize(P.fitems.size());
-    for (size_t i = 0; i < P.fitems.size(); ++i) P.f_list[i] = static_cast<int32_t>(i);
-}
-
-// Occurrence tiles: the transpose of the clause CSR. Occurrence (t, i) of variable v emits the
-// other literals of clause t in clause order (prefix then suffix of position i).
-gs_status build_var(const int64_t* clause_ptr, const int32_t* lits, HostPlan& P) {
-    const int64_t n = P.n;
-    std::vector<int64_t> occ_ptr(n + 1, 0);
-    std::vector<int32_t> clause_inst(P.m);
-    for (int32_t inst = 0; inst < P.n_inst; ++inst)
-        for (int64_t t = P.clause_off[inst]; t < P.clause_off[inst + 1]; ++t) clause_inst[t] = inst;
-    for (int64_t t = 0; t < P.m; ++t)
-        for (int64_t j = clause_ptr[t]; j < clause_ptr[t + 1]; ++j) occ_ptr[lit_row(P, clause_inst[t], lits[j]) + 1]++;
-    for (int64_t v = 0; v < n; ++v) occ_ptr[v + 1] += occ_ptr[v];
-    // occurrence -> literal index j (clause order per variable, by construction)
-    std::vector<int64_t> occ_lit(P.nnz);
-    {
-        std::vector<int64_t> fill(occ_ptr.begin(), occ_ptr.end() - 1);
-        for (int64_t t = 0; t < P.m; ++t)
-            for (int64_t j = clause_ptr[t]; j < clause_ptr[t + 1]; ++j)
-                occ_lit[fill[lit_row(P, clause_inst[t], lits[j])]++] = j;
-    }
-    std::vector<int64_t> lit_clause(P.nnz);
-    for (int64_t t = 0; t < P.m; ++t)
-        for (int64_t j = clause_ptr[t]; j < clause_ptr[t + 1]; ++j) lit_clause[j] = t;
-
-    auto occ_codes = [&](int64_t o) -> int {
-        const int64_t t = lit_clause[occ_lit[o]];
-        const int k = static_cast<int>(clause_ptr[t + 1] - clause_ptr[t]);
-        return k > 1 ? k - 1 : 1;
-    };
-    auto emit_occ = [&](int64_t o) {
-        const int64_t j = occ_lit[o];
-        const int64_t t = lit_clause[j];
-        const int32_t inst = clause_inst[t];
-        const int64_t a = clause_ptr[t], b = clause_ptr[t + 1];
-        const int32_t own = lits[j];
-        uint32_t tail = kVEnd;
-        if (own < 0) tail |= kVSelfNeg;
-        if (j == a) tail |= kVCredit;
-        if (b - a == 1) {
-            P.vcodes.push_back((kVSentinel << kVShift) | tail);
-            return;
-        }
-        const int64_t last = (j == b - 1) ? b - 2 : b - 1;
-        for (int64_t q = a; q < b; ++q) {
-            if (q == j) continue;
-            const int32_t l = lits[q];
-            uint32_t c = static_cast<uint32_t>(lit_row(P, inst, l)) << kVShift;
-            if (l < 0) c |= kVNeg;
-            if (q == last) c |= tail;
-            P.vcodes.push_back(c);
-        }
-    };
-    auto note_kk = [](int& acc, int k) { acc = (acc == -1) ? k : (acc == k ? acc : 0); };
-
-    struct Pending {
-        VarItem it;
-        int64_t cost;   // codes of the whole split variable (ordering key)
-    };
-    std::vector<Pending> light, split;
-
-    for (int32_t inst = 0; inst < P.n_inst; ++inst) {
-        const int64_t ra = P.var_off[inst], rb = P.var_off[inst + 1];
-        VarItem cur{};
-        bool open = false;
-        int cur_kk = -1;   // -1: no occurrence yet; 0: mixed widths
-        auto open_item = [&](int64_t v0) {
-            cur = VarItem{};
-            cur.code_base = static_cast<int64_t>(P.vcodes.size());
-            cur.rec_base = static_cast<int64_t>(P.vrecs.size());
-            cur.vtab_base = static_cast<int64_t>(P.vtab.size());
-            cur.v0 = static_cast<int32_t>(v0);
-            cur.split = -1;
-            cur.inst = inst;
-            open = true;
-            cur_kk = -1;
-        };
-        auto close_item = [&]() {
-            if (!open) return;
-            P.vtab.push_back((static_cast<uint32_t>(cur.n_occ) << 16) | static_cast<uint32_t>(cur.n_codes));
-            P.vrecs.push_back(static_cast<uint16_t>(cur.n_codes));
-            cur.kk = (cur_kk >= 1 && cur_kk <= 3) ? cur_kk : 0;
-            light.push_back({cur, 0});
-            open = false;
-        };
-        for (int64_t v = ra; v < rb; ++v) {
-            int64_t cost = 0;
-            for (int64_t o = occ_ptr[v]; o < occ_ptr[v + 1]; ++o) cost += occ_codes(o);
-            if (cost > kVarCodes) {
-                close_item();
-                // parts of <= kVarCodes codes, split at occurrence boundaries
-                std::vector<std::pair<int64_t, int64_t>> parts;
-                int64_t o = occ_ptr[v];
-                while (o < occ_ptr[v + 1]) {
-                    const int64_t o0 = o;
-                    int64_t c = 0;
-                    while (o < occ_ptr[v + 1] && c + occ_codes(o) <= kVarCodes) c += occ_codes(o++);
-                    parts.push_back({o0, o});
-                }
-                const int32_t slot = P.n_split++;
-                const int32_t row0 = P.n_split_rows;
-                P.n_split_rows += static_cast<int32_t>(parts.size());
-                for (size_t pi = 0; pi < parts.size(); ++pi) {
-                    VarItem it{};
-                    it.code_base = static_cast<int64_t>(P.vcodes.size());
-                    it.rec_base = static_cast<int64_t>(P.vrecs.size());
-                    it.vtab_base = static_cast<int64_t>(P.vtab.size());
-                    it.v0 = static_cast<int32_t>(v);
-                    it.nv = 1;
-                    it.split = slot;
-                    it.part = static_cast<int32_t>(pi);
-                    it.n_parts = static_cast<int32_t>(parts.size());
-                    it.split_row = row0;
-                    it.inst = inst;
-                    P.vtab.push_back(0u);
-                    int part_kk = -1;
-                    for (int64_t q = parts[pi].first; q < parts[pi].second; ++q) {
-                        P.vrecs.push_back(static_cast<uint16_t>(P.vcodes.size() - it.code_base));
-                        note_kk(part_kk, occ_codes(q));
-                        emit_occ(q);
-                        it.n_occ++;
-                    }
-                    it.kk = (part_kk >= 1 && part_kk <= 3) ? part_kk : 0;
-                    it.n_codes = static_cast<int32_t>(P.vcodes.size() - it.code_base);
-                    P.vrecs.push_back(static_cast<uint16_t>(it.n_codes));
-                    P.vtab.push_back((static_cast<uint32_t>(it.n_occ) << 16) | static_cast<uint32_t>(it.n_codes));
-                    split.push_back({it, cost});
-                }
-                continue;
-            }
-            if (open && (cur.nv == kVarVars || cur.n_codes + cost > kVarCodes)) close_item();
-            if (!open) open_item(v);
-            P.vtab.push_back((static_cast<uint32_t>(cur.n_occ) << 16) | static_cast<uint32_t>(cur.n_codes));
-            for (int64_t o = occ_ptr[v]; o < occ_ptr[v + 1]; ++o) {
-                P.vrecs.push_back(static_cast<uint16_t>(P.vcodes.size() - cur.code_base));
-                note_kk(cur_kk, occ_codes(o));
-                emit_occ(o);
-                cur.n_occ++;
-            }
-            cur.n_codes = static_cast<int32_t>(P.vcodes.size() - cur.code_base);
-            cur.nv++;
-        }
-        close_item();
-    }
-    // Schedule: parts of split variables first, largest variable first (they finish last
-    // otherwise), then whole-variable tiles in variable order.
-    std::stable_sort(split.begin(), split.end(), [](const Pending& a, const Pending& b) { return a.cost > b.cost; });
-    P.vitems.clear();
-    P.vitems.reserve(split.size() + light.size());
-    for (auto& s : split) P.vitems.push_back(s.it);
-    for (auto& l : light) P.vitems.push_back(l.it);
-    // per-instance lists, ascending tile id
-    std::vector<int32_t> cnt(P.n_inst + 1, 0);
-    for (auto& it : P.vitems) cnt[it.inst + 1]++;
-    for (int32_t i = 0; i < P.n_inst; ++i) cnt[i + 1] += cnt[i];
-    P.v_iptr = cnt;
-    P.v_list.resize(P.vitems.size());
-    std::vector<int32_t> fill(cnt.begin(), cnt.end() - 1);
-    for (size_t k = 0; k < P.vitems.size(); ++k) P.v_list[fill[P.vitems[k].inst]++] = static_cast<int32_t>(k);
-    return GS_OK;
-}
 
 template <typename T>
 gs_status upload(const std::vector<T>& h, T** d, int64_t* bytes, cudaStream_t s) {
@@ -508,15 +220,9 @@ AdamK adam_consts(const gs_adam& a, int64_t t) {
 
 gs_status build(int32_t n_inst, const int64_t* n_vars, const int64_t* n_clauses, const int64_t* clause_ptr,
                 const int32_t* lits, HostPlan& P) {
-    gs_status st = validate(n_inst, n_vars, n_clauses, clause_ptr, lits, P);
-    if (st != GS_OK) return st;
-    try {
-        build_fwd(clause_ptr, lits, P);
-        st = build_var(clause_ptr, lits, P);
-    } catch (const std::bad_alloc&) {
-        return fail(GS_ERR_OOM, "host allocation failed while building tiles");
-    }
-    return st;
+    std::string err;
+    const gs_status st = build_plan(n_inst, n_vars, n_clauses, clause_ptr, lits, P, &err);
+    return st == GS_OK ? GS_OK : fail(st, err);
 }
 
 gs_status load(int32_t n_inst, const int64_t* n_vars, const int64_t* n_clauses, const int64_t* clause_ptr,

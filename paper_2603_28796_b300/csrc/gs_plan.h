@@ -1,0 +1,39 @@
+// Host image of the device index structures and its builder (gs_plan.cpp). Internal to the
+// library; the layout of each array is described in gs_internal.h.
+#pragma once
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "gs.h"
+#include "gs_internal.h"
+
+namespace gs {
+
+struct HostPlan {
+    int64_t n = 0, m = 0, nnz = 0;
+    int32_t n_inst = 0, max_k = 0;
+    int64_t n_empty = 0, n_unit = 0, n_taut = 0, n_dup = 0;
+    std::vector<int64_t> var_off, clause_off, inst_empty;
+    // clause tiles
+    std::vector<uint32_t> fcodes;
+    std::vector<uint16_t> fctab;
+    std::vector<FwdItem> fitems;
+    // occurrence tiles
+    std::vector<uint32_t> vcodes;
+    std::vector<uint16_t> vrecs;
+    std::vector<uint32_t> vtab;
+    std::vector<VarItem> vitems;
+    int32_t n_split = 0, n_split_rows = 0;
+    // per-instance tile lists (ascending tile ids)
+    std::vector<int32_t> f_iptr, f_list, v_iptr, v_list;
+};
+
+// Validates a batch of formulas (instance-concatenated clause CSR, DIMACS literals local to
+// their instance) and builds the clause tiles and the occurrence tiles. The result depends only
+// on the input, never on the number of threads used. On failure returns the status and sets
+// *err to a one-line reason; P is then unspecified.
+gs_status build_plan(int32_t n_inst, const int64_t* n_vars, const int64_t* n_clauses, const int64_t* clause_ptr,
+                     const int32_t* lits, HostPlan& P, std::string* err);
+
+}  // namespace gs

@@ -109,3 +109,25 @@ def test_workload_catalogue_sizes():
     assert (w["plain"]["n"], w["plain"]["m"], w["plain"]["B"]) == (200, 852, 64)
     assert (w["precision"]["n"], w["precision"]["m"], w["precision"]["B"]) == (2_000_000, 8_000_000, 256)
     assert (w["structured"]["n"], w["structured"]["m"], w["structured"]["B"]) == (10_000_000, 42_000_000, 32)
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_inspect_statistics_random(seed):
+    """Loader statistics against a direct Python count on random formulas with empty, unit,
+    duplicated-literal and tautological clauses (the multi-threaded tile builder must see every
+    clause exactly once)."""
+    from tests import _brute
+    rng = np.random.default_rng(seed)
+    n = int(rng.integers(5, 3000))
+    clauses = _brute.random_clauses(rng, n, int(rng.integers(1, 20000)), 0, 9, distinct=bool(seed % 2))
+    cp, lits = _brute.csr_of(clauses)
+    info = _abi.gs_inspect_cnf(n, cp, lits)
+    widths = np.array([len(c) for c in clauses])
+    assert info["n_clauses"] == len(clauses) and info["nnz"] == widths.sum() and info["max_k"] == widths.max()
+    assert info["n_empty"] == (widths == 0).sum() and info["n_unit"] == (widths == 1).sum()
+    assert info["n_dup"] == sum(len(set(c)) < len(c) for c in clauses)
+    assert info["n_taut"] == sum(any(-l in c for l in c) for c in clauses)
+    assert info["n_occ_codes"] == int((widths * np.maximum(widths - 1, 1)).sum())
+    assert info["n_fwd_tiles"] >= -(-widths.sum() // 512)
+    used = np.unique(np.abs(lits))
+    assert info["n_var_tiles"] >= -(-len(used) // 64)
