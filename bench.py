@@ -43,6 +43,10 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle sample")
     ap.add_argument("--no-autotune", action="store_true", help="skip gs_autotune (use defaults / --var-* flags)")
+    ap.add_argument("--legs", default="precision,plain,structured",
+                    help="extra single-GPU measurements added to the line under 'legs' (comma list of precision, "
+                         "plain, structured, batching; 'none' for none)")
+    ap.add_argument("--leg-steps", type=int, default=50, help="timed steps of each extra leg")
     ap.add_argument("--var-lanes", type=int, default=0, help="cap on lanes per candidate chunk (gs_set_tuning)")
     ap.add_argument("--var-gather", type=int, default=0, help="0: automatic, 1: register loads, 2: TMA gather4 ring (gs_set_tuning)")
     return ap.parse_args()
@@ -158,6 +162,221 @@ def cpu_oracle_sample(cnf, B_sample, seed, target_s, max_steps=None):
     total = t1 + (time.perf_counter() - t0)
     steps += extra
     return cnf.nnz * B_sample * steps / total, total, steps, oracle.threads()
+
+
+# ---------------------------------------------------------------------------------------------
+# Extra single-GPU legs: the other workloads, each timed on its own problem after the headline.
+def _timed_steps(torch, eng, K, W):
+    """Mean ms per step (fused step + check) over K eager steps after W warm-up steps, and the
+    mean ms of the gs_step calls alone."""
+    from paper_2603_28796_b300 import _abi
+
+    for _ in range(max(3, W)):
+        eng.step()
+    torch.cuda.synchronize()
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(K)]
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record()
+    for k in range(K):
+        eng.t += 1
+        ev[k][0].record()
+        _abi.gs_step(eng.prob, eng.delta, eng.m, eng.v, eng.t, x_in=eng.x[eng.cur], x_out=eng.x[eng.cur ^ 1],
+                     loss=eng.loss, bits=eng.bits)
+        ev[k][1].record()
+        eng.cur ^= 1
+        _abi.gs_check_bits(eng.prob, eng.bits, eng.B, eng.unsat, eng.best)
+    t1.record()
+    torch.cuda.synchronize()
+    return t0.elapsed_time(t1) / K, statistics.mean(e[0].elapsed_time(e[1]) for e in ev)
+
+
+def _gather_model_bytes(nnz, n, B, s):
+    return nnz * B * 2 * s + n * B * (24 + s)
+
+
+def leg_precision(torch, args, peak):
+    """Mixed-width power-law workload: BF16 storage (the batched form) vs FP32 (the plain form)
+    on the same GPU, and the gradient error of the BF16 storage against the FP32 one at the same
+    logits (relative L2 norm over all coordinates and worst coordinate relative to the RMS)."""
+    from paper_2603_28796_b300 import _abi, synth
+    from paper_2603_28796_b300.engine import Engine, candidates
+
+    cnf, B, _, desc = workload_setup("precision")
+    prob = _abi.gs_load_cnf(cnf.n_vars, cnf.clause_ptr, cnf.lits)
+    n, nnz = cnf.n_vars, cnf.nnz
+    out = {"workload": desc, "n": n, "m": cnf.n_clauses, "nnz": nnz, "B": B}
+    for dtype, s in (("bf16", 2), ("f32", 4)):
+        tuning = _abi.gs_autotune(prob, B, dtype)
+        eng = Engine(prob, B, dtype, seed=11)
+        ms, step_ms = _timed_steps(torch, eng, args.leg_steps, args.warmup)
+        gm = _gather_model_bytes(nnz, B=B, n=n, s=s)
+        out[dtype] = {"ms_per_step": ms, "steps_per_s": 1000.0 / ms, "evals_per_s": nnz * B / (ms / 1000.0),
+                      "gs_step_ms": step_ms, "gather_model_GBps": gm / (step_ms / 1000.0) / 1e9,
+                      "gather_model_frac": gm / (step_ms / 1000.0) / 1e9 / peak, "tuning": tuning}
+        del eng
+        torch.cuda.empty_cache()
+    out["bf16_speedup"] = out["f32"]["ms_per_step"] / out["bf16"]["ms_per_step"]
+    delta = candidates(n, B)
+    delta.copy_(torch.from_numpy(synth.init_delta(n, B, seed=12)).cuda()[:, :B])
+    x32, x16 = candidates(n, B), candidates(n, B, torch.bfloat16)
+    _abi.gs_relax(prob, delta, x32)
+    _abi.gs_relax(prob, delta, x16)
+    g32 = _abi.gs_backward(prob, x32).double()
+    g16 = _abi.gs_backward(prob, x16).double()
+    diff = g16 - g32
+    rms = float(g32.pow(2).mean().sqrt())
+    out["grad_error_bf16_vs_f32"] = {
+        "rel_l2": float(diff.norm() / g32.norm()), "max_abs_over_rms": float(diff.abs().max()) / rms,
+        "sign_agreement": float(((g16 > 0) == (g32 > 0)).double().mean()),
+        "note": "gradients at the same float32 logits; x stored as BF16 (round to nearest even) vs FP32",
+    }
+    prob.close()
+    return out
+
+
+def leg_plain(torch, args):
+    """Plain method: n=200, m=852, B=64, 1000 steps captured in one CUDA graph (the whole
+    problem and state fit in L2, so this is launch- and latency-bound, not HBM-bound)."""
+    from paper_2603_28796_b300 import _abi
+    from paper_2603_28796_b300.engine import Engine
+
+    cnf, B, dtype, desc = workload_setup("plain")
+    prob = _abi.gs_load_cnf(cnf.n_vars, cnf.clause_ptr, cnf.lits)
+    tuning = _abi.gs_autotune(prob, B, dtype)
+    eng = Engine(prob, B, dtype, seed=5)
+    steps = 1000
+    eng.run(steps, graph=True)           # warm-up replay (capture included)
+    torch.cuda.synchronize()
+    g = eng.capture(steps)
+    torch.cuda.synchronize()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record()
+    g.replay()
+    t1.record()
+    torch.cuda.synchronize()
+    ms = t0.elapsed_time(t1)
+    unsat = eng.unsat.cpu().numpy()[0]
+    out = {"workload": desc, "steps": steps, "graph": True, "ms_total": ms, "us_per_step": 1000.0 * ms / steps,
+           "steps_per_s": 1000.0 * steps / ms, "evals_per_s": cnf.nnz * B * steps / (ms / 1000.0),
+           "solved_candidates": int((unsat == 0).sum()), "tuning": tuning,
+           "l2": "whole problem and state are L2-resident (1.7 MB); no flush"}
+    del g, eng
+    prob.close()
+    return out
+
+
+def leg_structured(torch, args, peak):
+    """Community-structured workload: n=10,000,000, m=42,000,000, k uniform 2..8, B=32, BF16."""
+    from paper_2603_28796_b300 import _abi
+    from paper_2603_28796_b300.engine import Engine
+
+    cnf, B, dtype, desc = workload_setup("structured")
+    prob = _abi.gs_load_cnf(cnf.n_vars, cnf.clause_ptr, cnf.lits)
+    tuning = _abi.gs_autotune(prob, B, dtype)
+    eng = Engine(prob, B, dtype, seed=21)
+    ms, step_ms = _timed_steps(torch, eng, args.leg_steps, args.warmup)
+    s = 2
+    gm = _gather_model_bytes(cnf.nnz, cnf.n_vars, B, s)
+    out = {"workload": desc, "n": cnf.n_vars, "m": cnf.n_clauses, "nnz": cnf.nnz, "B": B, "dtype": dtype,
+           "ms_per_step": ms, "steps_per_s": 1000.0 / ms, "evals_per_s": cnf.nnz * B / (ms / 1000.0),
+           "gs_step_ms": step_ms, "gather_model_GBps": gm / (step_ms / 1000.0) / 1e9,
+           "gather_model_frac": gm / (step_ms / 1000.0) / 1e9 / peak, "tuning": tuning}
+    del eng
+    prob.close()
+    torch.cuda.empty_cache()
+    return out
+
+
+def leg_batching(torch, args, peak):
+    """512 uneven instances, B=64 each: one batched problem stepped by one persistent launch
+    per kernel, vs a loop over 512 separately loaded problems stepping the same state rows."""
+    from paper_2603_28796_b300 import _abi
+    from paper_2603_28796_b300.engine import Engine
+
+    bt = workload_setup("batching")
+    batch, B, dtype, desc = bt
+    prob = _abi.gs_load_batch(batch.n_vars, batch.n_clauses, batch.clause_ptr, batch.lits)
+    tuning = _abi.gs_autotune(prob, B, dtype)
+    eng = Engine(prob, B, dtype, seed=31)
+    nnz, n = int(batch.clause_ptr[-1]), int(sum(batch.n_vars))
+    ms, step_ms = _timed_steps(torch, eng, max(5, args.leg_steps // 5), args.warmup)
+    gm = _gather_model_bytes(nnz, n, B, 4)
+    out = {"workload": desc, "n": n, "m": int(sum(batch.n_clauses)), "nnz": nnz, "B": B, "dtype": dtype,
+           "batched": {"ms_per_step": ms, "steps_per_s": 1000.0 / ms, "evals_per_s": nnz * B / (ms / 1000.0),
+                       "gs_step_ms": step_ms, "gather_model_frac": gm / (step_ms / 1000.0) / 1e9 / peak,
+                       "tuning": tuning}}
+    # per-instance loop over the same state rows
+    vo = np.concatenate([[0], np.cumsum(batch.n_vars)]).astype(np.int64)
+    co = np.concatenate([[0], np.cumsum(batch.n_clauses)]).astype(np.int64)
+    probs = []
+    for i in range(batch.n_inst):
+        a, b = batch.clause_ptr[co[i]], batch.clause_ptr[co[i + 1]]
+        probs.append(_abi.gs_load_cnf(int(batch.n_vars[i]), batch.clause_ptr[co[i]:co[i + 1] + 1] - a,
+                                      batch.lits[a:b]))
+        _abi.gs_reserve(probs[-1], B, dtype)
+    views = []
+    for i in range(batch.n_inst):
+        r0, r1 = vo[i], vo[i + 1]
+        # state rows are views of the batched buffers (256-byte rows); bit rows (8 bytes) of an
+        # instance need not start on a 16-byte boundary, so each instance gets its own
+        bits_i = torch.zeros((max(int(r1 - r0), 1), eng.nwd), dtype=torch.int64, device=eng.delta.device)
+        views.append((eng.delta[r0:r1], eng.m[r0:r1], eng.v[r0:r1], eng.x[0][r0:r1], eng.x[1][r0:r1],
+                      eng.loss[i:i + 1], bits_i, eng.unsat[i:i + 1], eng.best[i:i + 1]))
+
+    def loop_step():
+        eng.t += 1
+        for p, (d, mm, vv, x0, x1, lo, bi, un, be) in zip(probs, views):
+            xi, xo = (x0, x1) if eng.cur == 0 else (x1, x0)
+            _abi.gs_step(p, d, mm, vv, eng.t, x_in=xi, x_out=xo, loss=lo, bits=bi)
+            _abi.gs_check_bits(p, bi, B, un, be)
+        eng.cur ^= 1
+
+    for _ in range(3):
+        loop_step()
+    torch.cuda.synchronize()
+    K = max(5, args.leg_steps // 5)
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record()
+    for _ in range(K):
+        loop_step()
+    t1.record()
+    torch.cuda.synchronize()
+    ms_loop = t0.elapsed_time(t1) / K
+    out["per_instance_loop"] = {"ms_per_step": ms_loop, "steps_per_s": 1000.0 / ms_loop,
+                                "evals_per_s": nnz * B / (ms_loop / 1000.0), "launch": "eager"}
+    out["batched_speedup"] = ms_loop / ms
+    for p in probs:
+        p.close()
+    del eng
+    prob.close()
+    torch.cuda.empty_cache()
+    return out
+
+
+def run_legs(torch, args, peak):
+    names = [x for x in args.legs.split(",") if x and x != "none"]
+    legs = {}
+    for name in names:
+        t0 = time.perf_counter()
+        try:
+            if name == "precision":
+                legs[name] = leg_precision(torch, args, peak)
+            elif name == "plain":
+                legs[name] = leg_plain(torch, args)
+            elif name == "structured":
+                legs[name] = leg_structured(torch, args, peak)
+            elif name == "batching":
+                legs[name] = leg_batching(torch, args, peak)
+            else:
+                legs[name] = {"error": "unknown leg"}
+                continue
+        except Exception as e:   # a leg that cannot run (e.g. out of memory) is reported, not fatal
+            legs[name] = {"error": "%s: %s" % (type(e).__name__, e)}
+        legs[name]["wall_s"] = time.perf_counter() - t0
+    return legs
 
 
 # ---------------------------------------------------------------------------------------------
@@ -320,6 +539,13 @@ def run_native(args):
         e2e = {"value": evals_per_step * Ke * world / (e_ms / 1000.0), "unit": "evals/s",
                "h2d_bytes_per_step": n * B * 4, "d2h_bytes_per_step": B * 8 + B * 4, "steps": Ke}
 
+    legs = None
+    if rank == 0 and world == 1 and args.legs not in ("", "none"):
+        del eng
+        prob.close()
+        torch.cuda.empty_cache()
+        legs = run_legs(torch, args, peak)
+
     line = {
         "metric": "fwd+bwd clause-literal evals/s", "value": value, "unit": "evals/s", "n_gpus": world, "steps": K,
         "warmup": max(3, args.warmup), "ms_per_step": total_ms / K, "higher_is_better": True, "scaling": "weak",
@@ -329,7 +555,8 @@ def run_native(args):
                    "l2": "inputs larger than L2: x %.0f MB + delta/m/v %.0f MB per step" % (
                        n * B * s_bytes / 1e6, n * B * 12 / 1e6),
                    "steps_per_s": 1000.0 * K / total_ms, "tuning": tuning},
-        "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "gpu_launches": 4 * K,
+        "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "gpu_launches": 6 * K,
+        "legs": legs,
     }
     if rank == 0:
         print(json.dumps(line), flush=True)

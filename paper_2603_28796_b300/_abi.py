@@ -267,17 +267,23 @@ def gs_get_tuning(prob: Problem) -> dict:
     return {"var_lanes": int(t.var_lanes), "fwd_lanes": int(t.fwd_lanes), "var_gather": int(t.var_gather)}
 
 
+def _dtype_arg(dtype) -> int:
+    """A gs_dtype code from an int code, a name ("f32", "bf16", "f16") or a torch dtype."""
+    if isinstance(dtype, int):
+        return dtype
+    code = {"f32": GS_F32, "bf16": GS_BF16, "f16": GS_F16}.get(dtype) if isinstance(dtype, str) else None
+    return code if code is not None else _dtype_code(_torch().empty(0, dtype=dtype))
+
+
 def gs_autotune(prob: Problem, B: int, dtype, stream=None) -> dict:
-    code = dtype if isinstance(dtype, int) else {"f32": GS_F32, "bf16": GS_BF16, "f16": GS_F16}.get(dtype)
-    if code is None:
-        code = _dtype_code(_torch().empty(0, dtype=dtype))
+    code = _dtype_arg(dtype)
     t = GsTuning()
     _check(lib().gs_autotune(prob.handle, int(B), code, _stream(stream), ctypes.byref(t)), "gs_autotune")
     return {"var_lanes": int(t.var_lanes), "fwd_lanes": int(t.fwd_lanes), "var_gather": int(t.var_gather)}
 
 
 def gs_reserve(prob: Problem, B: int, dtype) -> None:
-    code = dtype if isinstance(dtype, int) else _dtype_code(_torch().empty(0, dtype=dtype))
+    code = _dtype_arg(dtype)
     _check(lib().gs_reserve(prob.handle, int(B), code), "gs_reserve")
 
 

@@ -173,3 +173,31 @@ def test_precision_workload_sampled_parity(dtype):
     tol = H.adam_tolerances(d0[:, S], z[:, S], z[:, S], g_ref, scale, t)
     out = dict(delta=H.host64(delta)[:, S], m=H.host64(m)[:, S], v=H.host64(v)[:, S])
     H.check_adam(out, dict(delta=d_ref, m=m_ref, v=v_ref), tol, "precision workload %s" % dtype)
+
+
+def test_precision_bf16_quantisation_error_bound():
+    """Stated error of the BF16 storage (the batched form) against the FP64 oracle at the FP32
+    master values: rounding x in [0, 1] to BF16 moves it by at most 2^-9, so each factor of a
+    leave-one-out product (all factors in [0, 1]) moves by at most 2^-9 and the product by at
+    most (k - 1) 2^-9; hence |g_bf16 - g| <= 2^-9 * sum over occurrences of v of (k_t - 1), plus
+    the float32 accumulation bound of the FP32 path."""
+    cnf, prob = workload("precision")
+    n, B = cnf.n_vars, 256
+    S = np.array([3, 77, 200])
+    d = synth.init_delta(n, B, seed=203)
+    delta = H.device_cands(d, B)
+    x32 = candidates(n, B)
+    x16 = candidates(n, B, torch.bfloat16)
+    _abi.gs_relax(prob, delta, x32)
+    _abi.gs_relax(prob, delta, x16)
+    g16 = H.host64(_abi.gs_backward(prob, x16))[:, S]
+    torch.cuda.synchronize()
+    g_ref, scale = oracle.backward(n, cnf.clause_ptr, cnf.lits, H.host64(x32)[:, S])
+    k = np.diff(cnf.clause_ptr)
+    owner = np.repeat(np.arange(cnf.n_clauses), k)
+    w = np.bincount(np.abs(cnf.lits) - 1, weights=np.maximum(k[owner] - 1, 0), minlength=n)
+    bound = 2.0 ** -9 * w[:, None] + 1e-5 * np.maximum(np.abs(g_ref), scale)
+    err = np.abs(g16 - g_ref)
+    assert np.all(err <= bound), float((err / np.maximum(bound, 1e-300)).max())
+    # and the error is far from vacuous: the relative L2 error is well below 1 %
+    assert np.linalg.norm(err) / np.linalg.norm(g_ref) < 1e-2
