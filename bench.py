@@ -39,6 +39,8 @@ def parse():
     ap.add_argument("--impl", choices=["native", "reference"], default="native")
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--dtype", default=None, help="override the storage dtype (f32, bf16, f16)")
+    ap.add_argument("--scale", type=float, default=1.0,
+                    help="shrink the workload's formula (n and m) by this factor, for profiling small cases")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle sample")
@@ -53,11 +55,11 @@ def parse():
 
 
 # ---------------------------------------------------------------------------------------------
-def workload_setup(name, dtype_override=None):
+def workload_setup(name, dtype_override=None, scale=1.0):
     from paper_2603_28796_b300 import synth
 
     w = synth.WORKLOADS[name]
-    cnf = synth.workload_cnf(name, seed=0)
+    cnf = synth.workload_cnf(name, seed=0, scale=scale)
     dtype = dtype_override or w["dtype"]
     return cnf, int(w["B"]), dtype, w["desc"]
 
@@ -384,7 +386,7 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
-    cnf, B, dtype, desc = workload_setup(args.workload, args.dtype)
+    cnf, B, dtype, desc = workload_setup(args.workload, args.dtype, args.scale)
     B_sample = 16
     import oracle
 
@@ -416,16 +418,15 @@ def run_native(args):
     from paper_2603_28796_b300 import _abi, synth
     from paper_2603_28796_b300.engine import Engine
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    if world > 1:
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl")
+    from paper_2603_28796_b300 import shard
+
+    rank, world, local = shard.init_from_env("nccl")
     dev = torch.device("cuda", local if world > 1 else 0)
     torch.cuda.set_device(dev)
 
-    cnf, B, dtype, desc = workload_setup(args.workload, args.dtype)
+    cnf, B, dtype, desc = workload_setup(args.workload, args.dtype, args.scale)
+    if args.scale != 1.0:
+        desc += " (formula scaled by %g: n=%d, m=%d)" % (args.scale, cnf.n_vars, cnf.n_clauses)
     prob = _abi.gs_load_cnf(cnf.n_vars, cnf.clause_ptr, cnf.lits)
     if args.var_lanes or args.var_gather:
         _abi.gs_set_tuning(prob, var_lanes=args.var_lanes, var_gather=args.var_gather)
@@ -433,7 +434,7 @@ def run_native(args):
         _abi.gs_autotune(prob, B, dtype)
     tuning = _abi.gs_get_tuning(prob)
     info = prob.info()
-    eng = Engine(prob, B, dtype, seed=1000 * rank + 1)
+    eng = Engine(prob, B, dtype, seed=shard.rank_seed(1, rank))
     nnz, n = cnf.nnz, cnf.n_vars
     evals_per_step = nnz * B
     s_bytes = {"f32": 4, "bf16": 2, "f16": 2}[dtype]
@@ -470,11 +471,12 @@ def run_native(args):
     total_ms = t_start.elapsed_time(t_end)
     step_ms = [ev[k][0].elapsed_time(ev[k][1]) for k in range(K)]
     check_ms = [ev[k][1].elapsed_time(ev[k][2]) for k in range(K)]
-    if world > 1:
-        tt = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        total_ms = float(tt.item())
+    total_ms = shard.max_over_ranks(total_ms, device=dev)
     _abi.gs_sync_status(prob)
+    # the run's one cross-rank exchange (outside the timed region): the best candidate over all
+    # ranks and its rounded assignment
+    b_rank, b_cand, b_unsat, _ = shard.global_best(eng.unsat, eng.best, eng.bits, n=cnf.n_vars)
+    best = {"unsat": b_unsat, "rank": b_rank, "candidate": b_cand, "of": B * world}
 
     value = evals_per_step * K * world / (total_ms / 1000.0)
     # roofline of the dominant kernel (fused variable-major pass inside gs_step)
@@ -532,10 +534,7 @@ def run_native(args):
         a1.record()
         torch.cuda.synchronize()
         e_ms = a0.elapsed_time(a1)
-        if world > 1:
-            tt = torch.tensor([e_ms], device=dev)
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            e_ms = float(tt.item())
+        e_ms = shard.max_over_ranks(e_ms, device=dev)
         e2e = {"value": evals_per_step * Ke * world / (e_ms / 1000.0), "unit": "evals/s",
                "h2d_bytes_per_step": n * B * 4, "d2h_bytes_per_step": B * 8 + B * 4, "steps": Ke}
 
@@ -554,7 +553,7 @@ def run_native(args):
                    "parallelism": "dp%d (independent candidate batches)" % world,
                    "l2": "inputs larger than L2: x %.0f MB + delta/m/v %.0f MB per step" % (
                        n * B * s_bytes / 1e6, n * B * 12 / 1e6),
-                   "steps_per_s": 1000.0 * K / total_ms, "tuning": tuning},
+                   "steps_per_s": 1000.0 * K / total_ms, "tuning": tuning, "best_after_run": best},
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "gpu_launches": 6 * K,
         "legs": legs,
     }

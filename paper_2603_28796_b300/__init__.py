@@ -3,7 +3,8 @@
 The compute path is ``libgaloissat.so`` (C ABI in ``include/gs.h``, sm_103a kernels); this
 package holds its Python binding (``_abi``, same function names as the C entry points), the
 training engine built on it (``engine``: autograd.Function, fused Adam step, CUDA-graph loop),
-the seeded input generators (``synth``) and the in-tree build (``build``).
+candidate sharding over ranks (``shard``), the seeded input generators (``synth``) and the
+in-tree build (``build``).
 
 Names of the binding are resolved on first use, so that importing the package (e.g. for the
 input generators) does not load the CUDA library.
