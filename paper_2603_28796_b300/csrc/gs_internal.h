@@ -197,8 +197,6 @@ cudaError_t launch_loss_reduce2(const float* part, int32_t bpad, const int32_t* 
 cudaError_t launch_count_reduce(const uint16_t* part16, int32_t bpad16, const int32_t* iptr, const int32_t* items,
                                 const int64_t* n_empty, int32_t n_inst, int32_t B, int32_t n_seg, int32_t* stage,
                                 int32_t* unsat, int32_t* best, cudaStream_t s);
-cudaError_t launch_finalize_check(int32_t* unsat, const int64_t* n_empty, int32_t n_inst, int32_t B,
-                                  int32_t* best, cudaStream_t s);
 cudaError_t launch_relax(const float* delta, void* x, int dtype, int64_t n, int32_t B, int64_t ldB,
                          float inv_tau, cudaStream_t s);
 cudaError_t launch_round(const float* delta, uint32_t* bits32, int64_t n, int32_t B, int64_t ldB,

@@ -1395,31 +1395,6 @@ __global__ void __launch_bounds__(256) k_loss_reduce(const float* part, int32_t 
     }
 }
 
-// Adds the always-unsatisfied empty clauses and picks the lowest candidate with the fewest
-// unsatisfied clauses, per instance.
-__global__ void __launch_bounds__(256) k_finalize_check(int32_t* unsat, const int64_t* n_empty, int32_t B,
-                                                        int32_t* best) {
-    __shared__ unsigned long long red[256];
-    const int inst = blockIdx.x;
-    int32_t* u = unsat + static_cast<int64_t>(inst) * B;
-    const int32_t add = static_cast<int32_t>(n_empty[inst]);
-    unsigned long long key = ~0ull;
-    for (int b = threadIdx.x; b < B; b += blockDim.x) {
-        const int32_t c = u[b] + add;
-        u[b] = c;
-        const unsigned long long k = (static_cast<unsigned long long>(static_cast<uint32_t>(c)) << 32) |
-                                     static_cast<uint32_t>(b);
-        key = k < key ? k : key;
-    }
-    red[threadIdx.x] = key;
-    __syncthreads();
-    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-        if (threadIdx.x < s && red[threadIdx.x + s] < red[threadIdx.x]) red[threadIdx.x] = red[threadIdx.x + s];
-        __syncthreads();
-    }
-    if (threadIdx.x == 0 && best) best[inst] = (B > 0) ? static_cast<int32_t>(red[0] & 0xffffffffull) : -1;
-}
-
 // Relaxed values x = sigma(delta / tau), written as T: one thread per 4 consecutive candidates of
 // a row (16-byte loads; the row stride keeps every group aligned), scalar tail past B.
 template <typename T>
@@ -1708,13 +1683,6 @@ cudaError_t launch_count_reduce(const uint16_t* part16, int32_t bpad16, const in
         k_reduce_tiles<uint16_t, int32_t><<<dim3((B + 31) / 32, n_inst, n_seg), 256, 0, s>>>(part16, bpad16, iptr,
                                                                                             items, B, n_seg, stage);
     k_count_final<<<n_inst, 1024, 0, s>>>(stage, B > 0 ? n_seg : 0, n_inst, n_empty, B, unsat, best);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_finalize_check(int32_t* unsat, const int64_t* n_empty, int32_t n_inst, int32_t B, int32_t* best,
-                                  cudaStream_t s) {
-    if (n_inst <= 0) return cudaSuccess;
-    k_finalize_check<<<n_inst, 256, 0, s>>>(unsat, n_empty, B, best);
     return cudaGetLastError();
 }
 
