@@ -51,7 +51,12 @@ def _load():
         lib.o_backward.argtypes = [i64, i64, dp, dp, i64, dp, dp, dp]
         lib.o_adam.argtypes = [i64, i64, dp, dp, dp, dp, i64, d, d, d, d, d, dp, dp, dp, dp]
         lib.o_round_check.argtypes = [i64, i64, dp, dp, i64, dp, dp, dp, dp]
-        for f in (lib.o_relax, lib.o_forward, lib.o_backward, lib.o_adam, lib.o_round_check):
+        u64 = ctypes.c_uint64
+        lib.o_philox4x64.argtypes = [i64, dp, dp, dp]
+        lib.o_logistic_noise.argtypes = [i64, i64, u64, i64, i64, dp, dp]
+        lib.o_st_adam.argtypes = [i64, i64, dp, dp, dp, dp, dp, i64, d, d, d, d, d, dp, dp, dp]
+        for f in (lib.o_relax, lib.o_forward, lib.o_backward, lib.o_adam, lib.o_round_check, lib.o_philox4x64,
+                  lib.o_logistic_noise, lib.o_st_adam):
             f.restype = ctypes.c_int
         _lib = lib
     return _lib
@@ -148,3 +153,54 @@ def step(n_vars, clause_ptr, lits, delta, m, v, x, t, lr=1.0, beta1=0.9, beta2=0
     g, s = backward(n_vars, clause_ptr, lits, x)
     d1, m1, v1, x1 = adam(delta, m, v, g, t, lr, beta1, beta2, eps, tau)
     return dict(loss=lu, grad=g, scale=s, delta=d1, m=m1, v=v1, x=x1)
+
+
+# ---------------------------------------------------------------------------------------------
+# Straight-through Gumbel training (Eq. 3 with noise, Eq. 4 in the forward pass); see oracle.c.
+def philox4x64(counter, key):
+    """Philox4x64-10 blocks: counter [..., 4] uint64, key [..., 2] uint64 -> [..., 4] uint64."""
+    c = np.ascontiguousarray(counter, dtype=np.uint64).reshape(-1, 4)
+    k = np.ascontiguousarray(key, dtype=np.uint64).reshape(-1, 2)
+    if k.shape[0] == 1 and c.shape[0] > 1:
+        k = np.ascontiguousarray(np.repeat(k, c.shape[0], axis=0))
+    out = np.empty_like(c)
+    _check(_load().o_philox4x64(c.shape[0], _ptr(c), _ptr(k), _ptr(out)), "philox4x64")
+    return out.reshape(np.shape(counter))
+
+
+def logistic_noise(n, B, seed, step, row0=0):
+    """(l [n, B] float64, k [n, B] uint32): the logistic noise of one step and its 23-bit draws."""
+    noise = np.empty((int(n), int(B)))
+    k23 = np.empty((int(n), int(B)), dtype=np.uint32)
+    _check(_load().o_logistic_noise(int(n), int(B), int(seed) & (2 ** 64 - 1), int(step), int(row0), _ptr(noise),
+                                    _ptr(k23)), "logistic_noise")
+    return noise, k23
+
+
+def st_adam(delta, m, v, grad_x, noise, step, lr=1.0, beta1=0.9, beta2=0.999, eps=1e-8, tau=1.0):
+    """Adam on delta with the straight-through chain y(1 - y)/tau, y = sigma((delta + noise)/tau)."""
+    d, mm, vv, g, ns = _f64(delta), _f64(m), _f64(v), _f64(grad_x), _f64(noise)
+    n, B = d.shape
+    d1, m1, v1 = (np.empty_like(d) for _ in range(3))
+    _check(_load().o_st_adam(n, B, _ptr(d), _ptr(mm), _ptr(vv), _ptr(g), _ptr(ns), int(step), float(lr),
+                             float(beta1), float(beta2), float(eps), float(tau), _ptr(d1), _ptr(m1), _ptr(v1)),
+           "st_adam")
+    return d1, m1, v1
+
+
+def st_step(n_vars, clause_ptr, lits, delta, m, v, noise, noise_next, t, lr=1.0, beta1=0.9, beta2=0.999,
+            eps=1e-8, tau=1.0):
+    """One straight-through Gumbel step at logits delta with this step's noise and the next's.
+
+    x_hat = [delta + noise > 0] (Eq. 4 on the noisy logits); loss = number of clauses false
+    under x_hat (L_unsat at a Boolean point); grad = dL/dx at x_hat (integers); Adam with the
+    chain through y = sigma((delta + noise)/tau); x_hat_next = [delta' + noise_next > 0].
+    Returns dict(x_hat, unsat, grad, delta, m, v, x_hat_next, unsat_next).
+    """
+    d = _f64(delta)
+    z = d + _f64(noise)
+    x_hat, unsat, _ = round_check(n_vars, clause_ptr, lits, z)
+    g, _ = backward(n_vars, clause_ptr, lits, x_hat.astype(np.float64))
+    d1, m1, v1 = st_adam(d, m, v, g, noise, t, lr, beta1, beta2, eps, tau)
+    x_next, unsat_next, _ = round_check(n_vars, clause_ptr, lits, d1 + _f64(noise_next))
+    return dict(x_hat=x_hat, unsat=unsat, grad=g, delta=d1, m=m1, v=v1, x_hat_next=x_next, unsat_next=unsat_next)

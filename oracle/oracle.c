@@ -214,3 +214,103 @@ int o_round_check(int64_t n, int64_t m, const int64_t* clause_ptr, const int32_t
     if (!x_hat) free(xb);
     return O_OK;
 }
+
+/*
+ * ---------------------------------------------------------------------------------------------
+ * Straight-through Gumbel training (Eq. 3 with noise, Eq. 4 in the forward pass).
+ *
+ * With two logits per variable, softmax((theta + g) / tau) puts y_1 = sigma((delta + l) / tau)
+ * on state 1, delta = theta_1 - theta_0 and l = g_1 - g_0. The difference of two independent
+ * Gumbel(0,1) variables is Logistic(0,1), so one logistic draw per (variable, candidate, step)
+ * carries exactly the noise of Eq. 3. The forward pass uses the hard assignment
+ * x_hat = argmax_j y_j = [delta + l > 0] (ties to state 0, Eq. 4); the backward pass takes the
+ * gradient of the loss at x_hat and passes it through the soft y_1 (straight-through):
+ *   dL/d delta = dL/dx (x_hat) * y_1 (1 - y_1) / tau.
+ *
+ * Noise generator (the draws are part of the method, so both sides implement one published
+ * counter-based generator): Philox4x64-10 of Salmon, Moraes, Dror and Shaw, "Parallel random
+ * numbers: as easy as 1, 2, 3" (SC'11), with key (seed, 0) and counter (row, b / 8, step, 0).
+ * The four 64-bit outputs give eight 32-bit halves; candidate b takes half (b & 1) of output
+ * (b >> 1) & 3. From a 32-bit half h: k = h >> 9 (23 bits), u = (k + 1/2) 2^-23 (exact in
+ * float32), l = log(u) - log(1 - u).
+ * ---------------------------------------------------------------------------------------------
+ */
+static void mul_hilo64(uint64_t a, uint64_t b, uint64_t* hi, uint64_t* lo) {
+    const unsigned __int128 p = (unsigned __int128)a * (unsigned __int128)b;
+    *hi = (uint64_t)(p >> 64);
+    *lo = (uint64_t)p;
+}
+
+static void philox4x64_10(const uint64_t ctr[4], const uint64_t key[2], uint64_t out[4]) {
+    const uint64_t M0 = 0xD2E7470EE14C6C93ULL, M1 = 0xCA5A826395121157ULL;   /* round multipliers */
+    const uint64_t W0 = 0x9E3779B97F4A7C15ULL, W1 = 0xBB67AE8584CAA73BULL;   /* Weyl key increments */
+    uint64_t x0 = ctr[0], x1 = ctr[1], x2 = ctr[2], x3 = ctr[3];
+    uint64_t k0 = key[0], k1 = key[1];
+    for (int r = 0; r < 10; r++) {
+        uint64_t hi0, lo0, hi1, lo1;
+        mul_hilo64(M0, x0, &hi0, &lo0);
+        mul_hilo64(M1, x2, &hi1, &lo1);
+        const uint64_t y0 = hi1 ^ x1 ^ k0, y1 = lo1, y2 = hi0 ^ x3 ^ k1, y3 = lo0;
+        x0 = y0; x1 = y1; x2 = y2; x3 = y3;
+        k0 += W0;
+        k1 += W1;
+    }
+    out[0] = x0; out[1] = x1; out[2] = x2; out[3] = x3;
+}
+
+/* One Philox4x64-10 block per (counter, key) pair: ctr [count][4], key [count][2], out [count][4]. */
+int o_philox4x64(int64_t count, const uint64_t* ctr, const uint64_t* key, uint64_t* out) {
+    if (count < 0) return O_BAD_ARG;
+    for (int64_t i = 0; i < count; i++) philox4x64_10(ctr + 4 * i, key + 2 * i, out + 4 * i);
+    return O_OK;
+}
+
+/*
+ * Logistic noise l[v * B + b] for rows row0 .. row0 + n - 1 (row = variable row of the batch)
+ * of step `step`, and optionally the 23-bit integers k it came from.
+ */
+int o_logistic_noise(int64_t n, int64_t B, uint64_t seed, int64_t step, int64_t row0, double* noise,
+                     uint32_t* k23) {
+    if (n < 0 || B < 0 || row0 < 0) return O_BAD_ARG;
+#pragma omp parallel for schedule(static)
+    for (int64_t v = 0; v < n; v++) {
+        for (int64_t b = 0; b < B; b++) {
+            const uint64_t ctr[4] = {(uint64_t)(row0 + v), (uint64_t)(b >> 3), (uint64_t)step, 0};
+            const uint64_t key[2] = {seed, 0};
+            uint64_t r[4];
+            philox4x64_10(ctr, key, r);
+            const uint64_t word = r[(b >> 1) & 3];
+            const uint32_t h = (uint32_t)((b & 1) ? (word >> 32) : (word & 0xffffffffULL));
+            const uint32_t k = h >> 9;
+            const double u = ((double)k + 0.5) / 8388608.0;   /* 2^23 */
+            noise[v * B + b] = log(u) - log(1.0 - u);
+            if (k23) k23[v * B + b] = k;
+        }
+    }
+    return O_OK;
+}
+
+/*
+ * Adam step of the straight-through Gumbel form: gx = dL/dx at the hard point x_hat, noise l of
+ * the same step; z = (delta + l) / tau, y = sigma(z), g = gx * y (1 - y) / tau, then the Adam
+ * update of o_adam. Outputs may alias inputs element-wise.
+ */
+int o_st_adam(int64_t n, int64_t B, const double* delta, const double* m, const double* v, const double* gx,
+              const double* noise, int64_t step, double lr, double beta1, double beta2, double eps, double tau,
+              double* delta_out, double* m_out, double* v_out) {
+    if (n < 0 || B < 0 || step < 1 || !(tau > 0.0)) return O_BAD_ARG;
+    const double bc1 = 1.0 - pow(beta1, (double)step);
+    const double bc2 = 1.0 - pow(beta2, (double)step);
+    for (int64_t i = 0; i < n * B; i++) {
+        const double z = (delta[i] + noise[i]) / tau;
+        const double y = 1.0 / (1.0 + exp(-z));
+        const double one_minus_y = 1.0 / (1.0 + exp(z));
+        const double g = gx[i] * y * one_minus_y / tau;
+        const double m1 = beta1 * m[i] + (1.0 - beta1) * g;
+        const double v1 = beta2 * v[i] + (1.0 - beta2) * g * g;
+        m_out[i] = m1;
+        v_out[i] = v1;
+        delta_out[i] = delta[i] - lr * (m1 / bc1) / (sqrt(v1 / bc2) + eps);
+    }
+    return O_OK;
+}
