@@ -45,8 +45,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle sample")
     ap.add_argument("--no-autotune", action="store_true", help="skip gs_autotune (use defaults / --var-* flags)")
-    ap.add_argument("--legs", default="precision,plain,structured",
-                    help="extra single-GPU measurements added to the line under 'legs' (comma list of precision, "
+    ap.add_argument("--legs", default="st,precision,plain,structured",
+                    help="extra single-GPU measurements added to the line under 'legs' (comma list of st, precision, "
                          "plain, structured, batching; 'none' for none)")
     ap.add_argument("--leg-steps", type=int, default=50, help="timed steps of each extra leg")
     ap.add_argument("--var-lanes", type=int, default=0, help="cap on lanes per candidate chunk (gs_set_tuning)")
@@ -358,6 +358,49 @@ def leg_batching(torch, args, peak):
     return out
 
 
+def leg_st(torch, args, peak):
+    """The paper's own training forward on the differentiation workload: straight-through Gumbel
+    (hard assignment in the forward pass, soft chain in the backward pass, noise drawn in the
+    kernel). One step = gs_check_bits on the hard assignment (the loss) + gs_st_step."""
+    from paper_2603_28796_b300 import _abi
+    from paper_2603_28796_b300.engine import STEngine
+
+    cnf, B, _, desc = workload_setup("differentiation")
+    prob = _abi.gs_load_cnf(cnf.n_vars, cnf.clause_ptr, cnf.lits)
+    eng = STEngine(prob, B, seed=41, noise_seed=43)
+    for _ in range(max(3, args.warmup)):
+        eng.step()
+    torch.cuda.synchronize()
+    K = max(args.leg_steps, 20)
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(K)]
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record()
+    for k in range(K):
+        eng.t += 1
+        _abi.gs_check_bits(prob, eng.bits[eng.cur], B, eng.unsat, eng.best)
+        ev[k][0].record()
+        _abi.gs_st_step(prob, eng.delta, eng.m, eng.v, eng.bits[eng.cur], eng.bits[eng.cur ^ 1], eng.t,
+                        seed=eng.noise_seed, noise=eng.noise[eng.cur], noise_next_out=eng.noise[eng.cur ^ 1])
+        ev[k][1].record()
+        eng.cur ^= 1
+    t1.record()
+    torch.cuda.synchronize()
+    ms = t0.elapsed_time(t1) / K
+    st_ms = statistics.mean(e[0].elapsed_time(e[1]) for e in ev)
+    n, nnz = cnf.n_vars, cnf.nnz
+    compulsory = n * B * (24 + 8) + n * ((B + 63) // 64) * 8     # delta, m, v + noise ring + bits
+    out = {"workload": desc + ", straight-through Gumbel", "ms_per_step": ms, "steps_per_s": 1000.0 / ms,
+           "evals_per_s": nnz * B / (ms / 1000.0), "st_step_ms": st_ms,
+           "compulsory_bytes": compulsory, "compulsory_GBps": compulsory / (st_ms / 1000.0) / 1e9,
+           "compulsory_frac": compulsory / (st_ms / 1000.0) / 1e9 / peak,
+           "median_unsat": float(np.median(eng.unsat.cpu().numpy()[0]))}
+    del eng
+    prob.close()
+    torch.cuda.empty_cache()
+    return out
+
+
 def run_legs(torch, args, peak):
     names = [x for x in args.legs.split(",") if x and x != "none"]
     legs = {}
@@ -370,6 +413,8 @@ def run_legs(torch, args, peak):
                 legs[name] = leg_plain(torch, args)
             elif name == "structured":
                 legs[name] = leg_structured(torch, args, peak)
+            elif name == "st":
+                legs[name] = leg_st(torch, args, peak)
             elif name == "batching":
                 legs[name] = leg_batching(torch, args, peak)
             else:

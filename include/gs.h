@@ -283,6 +283,62 @@ gs_status gs_check_bits(gs_problem* prob, const uint64_t* bits, int32_t B, int32
                         gs_stream stream);
 
 /*
+ * Straight-through Gumbel training (Sec. "Gradient-based Optimization with Gumbel-Softmax":
+ * Eq. 3 with noise, Eq. 4 in the forward pass). With two logits per variable, Eq. 3 puts
+ * y = sigma((delta + l) / tau) on state 1, delta = theta_1 - theta_0 and l = g_1 - g_0, which is
+ * Logistic(0,1) for independent Gumbel(0,1) draws g. The forward pass uses the hard assignment
+ * x_hat = [delta + l > 0] (ties to state 0); the backward pass takes dL/dx at x_hat (an integer:
+ * negated occurrences of the variable whose other literals are all false, minus positive ones)
+ * through the soft y: dL/d delta = dL/dx(x_hat) * y (1 - y) / tau. The loss at x_hat is the
+ * number of unsatisfied clauses (gs_check_bits on x_hat).
+ *
+ * Noise: Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11) with key (seed mod 2^32, seed / 2^32)
+ * and counter (b / 4, row, step mod 2^32, step / 2^32); candidate b takes output word b % 4;
+ * k = word >> 9, u = (k + 1/2) 2^-23, l = log(u / (1 - u)) in float32. Rows are the batch's
+ * variable rows (instances concatenated). The decision [delta + l > 0] in float32 is exact.
+ */
+
+/*
+ * gs_st_noise - the logistic noise l of one step into noise, device float [n][ldB] (every
+ * (v, b < B) written; 16-byte aligned; ldB a multiple of 4). step >= 0.
+ * Errors: GS_ERR_INVALID_ARG, GS_ERR_STATE, GS_ERR_CUDA.
+ */
+gs_status gs_st_noise(gs_problem* prob, uint64_t seed, int64_t step, float* noise, int32_t B, int64_t ldB,
+                      gs_stream stream);
+
+/*
+ * gs_st_sample - hard assignment of a step: bits = [delta + l > 0] (Eq. 4 on the noisy logits).
+ *   delta  device float [n][ldB].
+ *   noise  device float [n][ldB] holding l, or NULL: l generated from (seed, step) as above.
+ *   bits   device uint64 [n][ceil(B/64)] (output; bits >= B are 0).
+ * Errors: GS_ERR_INVALID_ARG, GS_ERR_STATE, GS_ERR_CUDA.
+ */
+gs_status gs_st_sample(gs_problem* prob, const float* delta, const float* noise, uint64_t seed, int64_t step,
+                       int32_t B, int64_t ldB, uint64_t* bits, gs_stream stream);
+
+/*
+ * gs_st_step - one straight-through Gumbel training step t, in place:
+ *   gx = dL/dx at bits_in (the hard assignment of step t, from gs_st_sample or the previous
+ *   gs_st_step), y = sigma((delta + l_t)/tau), g = gx y (1 - y) / tau, Adam on delta exactly as
+ *   gs_step, then bits_out = [delta' + l_{t+1} > 0], the hard assignment of step t + 1.
+ *   delta, m, v          device float [n][ldB], read and written.
+ *   bits_in              device uint64 [n][ceil(B/64)], read; bits_out the same shape, written
+ *                        (every row; bits >= B are 0); they must not overlap.
+ *   noise, noise_next    device float [n][ldB] holding l_t and l_{t+1}, or NULL: generated from
+ *                        (seed, step) and (seed, step + 1) inside the kernel.
+ *   noise_next_out       device float [n][ldB] receiving the generated l_{t+1} (noise_next must
+ *                        be NULL), or NULL. Passing it back as the next step's noise draws each
+ *                        value once instead of twice (a two-buffer ring).
+ *   step                 1-based Adam step t (bias correction) and noise counter.
+ * Gathers one bit per (literal, candidate): each variable's gradient is a signed bit-sliced
+ * count over its occurrence list (no atomics).
+ * Errors: GS_ERR_INVALID_ARG, GS_ERR_STATE, GS_ERR_CUDA.
+ */
+gs_status gs_st_step(gs_problem* prob, float* delta, float* m, float* v, const uint64_t* bits_in, uint64_t* bits_out,
+                     const float* noise, const float* noise_next, float* noise_next_out, uint64_t seed, int64_t step,
+                     int32_t B, int64_t ldB, const gs_adam* adam, gs_stream stream);
+
+/*
  * gs_wait_selftest - exercises the device-side failure path: one warp waits on a barrier phase
  * that nothing completes, gives up after limit_us microseconds (1..1e7) and records
  * GS_ERR_TIMEOUT in the problem's sticky status, exactly as a stalled tile copy would. No

@@ -52,10 +52,10 @@ def _load():
         lib.o_adam.argtypes = [i64, i64, dp, dp, dp, dp, i64, d, d, d, d, d, dp, dp, dp, dp]
         lib.o_round_check.argtypes = [i64, i64, dp, dp, i64, dp, dp, dp, dp]
         u64 = ctypes.c_uint64
-        lib.o_philox4x64.argtypes = [i64, dp, dp, dp]
+        lib.o_philox4x32.argtypes = [i64, dp, dp, dp]
         lib.o_logistic_noise.argtypes = [i64, i64, u64, i64, i64, dp, dp]
         lib.o_st_adam.argtypes = [i64, i64, dp, dp, dp, dp, dp, i64, d, d, d, d, d, dp, dp, dp]
-        for f in (lib.o_relax, lib.o_forward, lib.o_backward, lib.o_adam, lib.o_round_check, lib.o_philox4x64,
+        for f in (lib.o_relax, lib.o_forward, lib.o_backward, lib.o_adam, lib.o_round_check, lib.o_philox4x32,
                   lib.o_logistic_noise, lib.o_st_adam):
             f.restype = ctypes.c_int
         _lib = lib
@@ -157,14 +157,14 @@ def step(n_vars, clause_ptr, lits, delta, m, v, x, t, lr=1.0, beta1=0.9, beta2=0
 
 # ---------------------------------------------------------------------------------------------
 # Straight-through Gumbel training (Eq. 3 with noise, Eq. 4 in the forward pass); see oracle.c.
-def philox4x64(counter, key):
-    """Philox4x64-10 blocks: counter [..., 4] uint64, key [..., 2] uint64 -> [..., 4] uint64."""
-    c = np.ascontiguousarray(counter, dtype=np.uint64).reshape(-1, 4)
-    k = np.ascontiguousarray(key, dtype=np.uint64).reshape(-1, 2)
+def philox4x32(counter, key):
+    """Philox4x32-10 blocks: counter [..., 4] uint32, key [..., 2] uint32 -> [..., 4] uint32."""
+    c = np.ascontiguousarray(counter, dtype=np.uint32).reshape(-1, 4)
+    k = np.ascontiguousarray(key, dtype=np.uint32).reshape(-1, 2)
     if k.shape[0] == 1 and c.shape[0] > 1:
         k = np.ascontiguousarray(np.repeat(k, c.shape[0], axis=0))
     out = np.empty_like(c)
-    _check(_load().o_philox4x64(c.shape[0], _ptr(c), _ptr(k), _ptr(out)), "philox4x64")
+    _check(_load().o_philox4x32(c.shape[0], _ptr(c), _ptr(k), _ptr(out)), "philox4x32")
     return out.reshape(np.shape(counter))
 
 

@@ -228,29 +228,22 @@ int o_round_check(int64_t n, int64_t m, const int64_t* clause_ptr, const int32_t
  *   dL/d delta = dL/dx (x_hat) * y_1 (1 - y_1) / tau.
  *
  * Noise generator (the draws are part of the method, so both sides implement one published
- * counter-based generator): Philox4x64-10 of Salmon, Moraes, Dror and Shaw, "Parallel random
- * numbers: as easy as 1, 2, 3" (SC'11), with key (seed, 0) and counter (row, b / 8, step, 0).
- * The four 64-bit outputs give eight 32-bit halves; candidate b takes half (b & 1) of output
- * (b >> 1) & 3. From a 32-bit half h: k = h >> 9 (23 bits), u = (k + 1/2) 2^-23 (exact in
- * float32), l = log(u) - log(1 - u).
+ * counter-based generator): Philox4x32-10 of Salmon, Moraes, Dror and Shaw, "Parallel random
+ * numbers: as easy as 1, 2, 3" (SC'11), with key (seed mod 2^32, seed / 2^32) and counter
+ * (b / 4, row, step mod 2^32, step / 2^32); candidate b takes output word b % 4. From a 32-bit
+ * word h: k = h >> 9 (23 bits), u = (k + 1/2) 2^-23 (exact in float32), l = log(u / (1 - u)).
  * ---------------------------------------------------------------------------------------------
  */
-static void mul_hilo64(uint64_t a, uint64_t b, uint64_t* hi, uint64_t* lo) {
-    const unsigned __int128 p = (unsigned __int128)a * (unsigned __int128)b;
-    *hi = (uint64_t)(p >> 64);
-    *lo = (uint64_t)p;
-}
-
-static void philox4x64_10(const uint64_t ctr[4], const uint64_t key[2], uint64_t out[4]) {
-    const uint64_t M0 = 0xD2E7470EE14C6C93ULL, M1 = 0xCA5A826395121157ULL;   /* round multipliers */
-    const uint64_t W0 = 0x9E3779B97F4A7C15ULL, W1 = 0xBB67AE8584CAA73BULL;   /* Weyl key increments */
-    uint64_t x0 = ctr[0], x1 = ctr[1], x2 = ctr[2], x3 = ctr[3];
-    uint64_t k0 = key[0], k1 = key[1];
+static void philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]) {
+    const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;   /* round multipliers */
+    const uint32_t W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;   /* Weyl key increments */
+    uint32_t x0 = ctr[0], x1 = ctr[1], x2 = ctr[2], x3 = ctr[3];
+    uint32_t k0 = key[0], k1 = key[1];
     for (int r = 0; r < 10; r++) {
-        uint64_t hi0, lo0, hi1, lo1;
-        mul_hilo64(M0, x0, &hi0, &lo0);
-        mul_hilo64(M1, x2, &hi1, &lo1);
-        const uint64_t y0 = hi1 ^ x1 ^ k0, y1 = lo1, y2 = hi0 ^ x3 ^ k1, y3 = lo0;
+        const uint64_t p0 = (uint64_t)M0 * x0, p1 = (uint64_t)M1 * x2;
+        const uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+        const uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+        const uint32_t y0 = hi1 ^ x1 ^ k0, y1 = lo1, y2 = hi0 ^ x3 ^ k1, y3 = lo0;
         x0 = y0; x1 = y1; x2 = y2; x3 = y3;
         k0 += W0;
         k1 += W1;
@@ -258,10 +251,10 @@ static void philox4x64_10(const uint64_t ctr[4], const uint64_t key[2], uint64_t
     out[0] = x0; out[1] = x1; out[2] = x2; out[3] = x3;
 }
 
-/* One Philox4x64-10 block per (counter, key) pair: ctr [count][4], key [count][2], out [count][4]. */
-int o_philox4x64(int64_t count, const uint64_t* ctr, const uint64_t* key, uint64_t* out) {
+/* One Philox4x32-10 block per (counter, key) pair: ctr [count][4], key [count][2], out [count][4]. */
+int o_philox4x32(int64_t count, const uint32_t* ctr, const uint32_t* key, uint32_t* out) {
     if (count < 0) return O_BAD_ARG;
-    for (int64_t i = 0; i < count; i++) philox4x64_10(ctr + 4 * i, key + 2 * i, out + 4 * i);
+    for (int64_t i = 0; i < count; i++) philox4x32_10(ctr + 4 * i, key + 2 * i, out + 4 * i);
     return O_OK;
 }
 
@@ -275,15 +268,14 @@ int o_logistic_noise(int64_t n, int64_t B, uint64_t seed, int64_t step, int64_t 
 #pragma omp parallel for schedule(static)
     for (int64_t v = 0; v < n; v++) {
         for (int64_t b = 0; b < B; b++) {
-            const uint64_t ctr[4] = {(uint64_t)(row0 + v), (uint64_t)(b >> 3), (uint64_t)step, 0};
-            const uint64_t key[2] = {seed, 0};
-            uint64_t r[4];
-            philox4x64_10(ctr, key, r);
-            const uint64_t word = r[(b >> 1) & 3];
-            const uint32_t h = (uint32_t)((b & 1) ? (word >> 32) : (word & 0xffffffffULL));
-            const uint32_t k = h >> 9;
+            const uint64_t row = (uint64_t)(row0 + v), st = (uint64_t)step;
+            const uint32_t ctr[4] = {(uint32_t)(b >> 2), (uint32_t)row, (uint32_t)st, (uint32_t)(st >> 32)};
+            const uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+            uint32_t r[4];
+            philox4x32_10(ctr, key, r);
+            const uint32_t k = r[b & 3] >> 9;
             const double u = ((double)k + 0.5) / 8388608.0;   /* 2^23 */
-            noise[v * B + b] = log(u) - log(1.0 - u);
+            noise[v * B + b] = log(u / (1.0 - u));
             if (k23) k23[v * B + b] = k;
         }
     }

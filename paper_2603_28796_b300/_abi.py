@@ -28,6 +28,7 @@ STATUS_NAMES = {
 EXPORTED = (
     "gs_adam_default", "gs_load_cnf", "gs_load_batch", "gs_load_dimacs", "gs_inspect_cnf", "gs_info_get",
     "gs_set_tuning", "gs_get_tuning", "gs_autotune", "gs_reserve", "gs_relax", "gs_forward", "gs_forward_noalloc", "gs_backward", "gs_step", "gs_round_check", "gs_check_bits",
+    "gs_st_noise", "gs_st_sample", "gs_st_step",
     "gs_wait_selftest", "gs_sync_status", "gs_free", "gs_status_str", "gs_last_error",
 )
 
@@ -99,6 +100,10 @@ def lib():
                                        ctypes.POINTER(GsAdam), vp, vp, vp]),
             "gs_round_check": (ctypes.c_int, [vp, vp, i32, i64, vp, vp, vp, vp]),
             "gs_check_bits": (ctypes.c_int, [vp, vp, i32, vp, vp, vp]),
+            "gs_st_noise": (ctypes.c_int, [vp, ctypes.c_uint64, i64, vp, i32, i64, vp]),
+            "gs_st_sample": (ctypes.c_int, [vp, vp, vp, ctypes.c_uint64, i64, i32, i64, vp, vp]),
+            "gs_st_step": (ctypes.c_int, [vp, vp, vp, vp, vp, vp, vp, vp, vp, ctypes.c_uint64, i64, i32, i64,
+                                          ctypes.POINTER(GsAdam), vp]),
             "gs_wait_selftest": (ctypes.c_int, [vp, ctypes.c_uint32, vp]),
             "gs_sync_status": (ctypes.c_int, [vp]),
             "gs_free": (None, [vp]),
@@ -381,6 +386,43 @@ def gs_check_bits(prob: Problem, bits, B: int, unsat=None, best=None, stream=Non
     _check(lib().gs_check_bits(prob.handle, _ptr(bits), int(B), _ptr(unsat), _ptr(best), _stream(stream)),
            "gs_check_bits")
     return unsat, best
+
+
+# ------------------------------------------------------------------------------------------
+# Straight-through Gumbel training (Eq. 3 with noise, Eq. 4 in the forward pass).
+def _seed(seed) -> int:
+    return int(seed) & (2 ** 64 - 1)
+
+
+def gs_st_noise(prob: Problem, seed: int, step: int, noise, stream=None) -> None:
+    """Logistic noise l of one step into a float32 [n, B] candidate tensor."""
+    B, ldB = _cand(noise, "noise", prob.n_vars)
+    _check(lib().gs_st_noise(prob.handle, _seed(seed), int(step), _ptr(noise), B, ldB, _stream(stream)),
+           "gs_st_noise")
+
+
+def gs_st_sample(prob: Problem, delta, bits, seed: int = 0, step: int = 1, noise=None, stream=None) -> None:
+    """bits = [delta + l > 0] (l from ``noise`` or generated from (seed, step))."""
+    B, ldB = _cand(delta, "delta", prob.n_vars)
+    if noise is not None and _cand(noise, "noise", prob.n_vars) != (B, ldB):
+        raise ValueError("noise must have the same B and ldB as delta")
+    _check(lib().gs_st_sample(prob.handle, _ptr(delta), _ptr(noise), _seed(seed), int(step), B, ldB, _ptr(bits),
+                              _stream(stream)), "gs_st_sample")
+
+
+def gs_st_step(prob: Problem, delta, m, v, bits_in, bits_out, step: int, seed: int = 0, noise=None, noise_next=None,
+               noise_next_out=None, adam=None, stream=None) -> None:
+    """One straight-through Gumbel step t: gradient at the hard point bits_in, soft chain, Adam,
+    bits_out = [delta' + l_{t+1} > 0]. noise / noise_next: float32 [n, B] tensors or None
+    (generated); noise_next_out receives the generated l_{t+1}."""
+    B, ldB = _cand(delta, "delta", prob.n_vars)
+    for t, name in ((m, "m"), (v, "v"), (noise, "noise"), (noise_next, "noise_next"), (noise_next_out, "noise_next_out")):
+        if t is not None and _cand(t, name, prob.n_vars) != (B, ldB):
+            raise ValueError("%s must have the same B and ldB as delta" % name)
+    a = _adam(adam)
+    _check(lib().gs_st_step(prob.handle, _ptr(delta), _ptr(m), _ptr(v), _ptr(bits_in), _ptr(bits_out), _ptr(noise),
+                            _ptr(noise_next), _ptr(noise_next_out), _seed(seed), int(step), B, ldB,
+                            ctypes.byref(a) if a is not None else None, _stream(stream)), "gs_st_step")
 
 
 def gs_wait_selftest(prob: Problem, limit_us: int = 1000, stream=None) -> None:

@@ -367,6 +367,30 @@ bool encode_rows_map(CUtensorMap* tm, const void* x, int dtype, int64_t n, int32
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// Straight-through pass chunking: one 32-bit word (32 candidates) per lane, LW lanes per chunk.
+struct StChunking {
+    int lw, nw32, n_chunks, bpad;
+};
+StChunking st_chunking(int32_t B) {
+    StChunking c{};
+    c.nw32 = 2 * nwords(B);
+    c.lw = 1;
+    while (c.lw < c.nw32 && c.lw < 32) c.lw *= 2;
+    c.n_chunks = std::max(1, (c.nw32 + c.lw - 1) / c.lw);
+    c.bpad = c.n_chunks * c.lw * 32;
+    return c;
+}
+
+gs_status ensure_st_ws(gs_problem* p, int32_t B, cudaStream_t s) {
+    const bool cap = capturing(s);
+    const StChunking c = st_chunking(B);
+    gs_status st;
+    if ((st = grow(&p->split, &p->split_cap, std::max<size_t>(1, static_cast<size_t>(p->h.n_split_rows) * c.bpad), s,
+                   cap, "split partials")) != GS_OK)
+        return st;
+    return grow(&p->ctl, &p->ctl_cap, 4 + static_cast<size_t>(p->h.n_split) * c.n_chunks, s, cap, "counters");
+}
+
 gs_status var_pass(gs_problem* p, int mode, const void* x_in, int dtype, int32_t B, int64_t ldB, const double* dloss,
                    float* grad, float* delta, float* m, float* v, void* x_out, const AdamK* k, double* loss,
                    uint64_t* bits, cudaStream_t s) {
@@ -682,6 +706,10 @@ gs_status gs_reserve(gs_problem* p, int32_t B, gs_dtype dtype) {
     tensor_map_encoder();
     grid_forward(dtype, cf.lc);
     grid_check(lanes_for_words(nwords(B)));
+    if (dtype == GS_F32) {
+        if ((st = ensure_st_ws(p, B, nullptr)) != GS_OK) return st;
+        grid_st_pass(st_chunking(B).lw);
+    }
     GS_CUDA(cudaDeviceSynchronize(), "cudaDeviceSynchronize");
     return GS_OK;
 }
@@ -938,5 +966,112 @@ extern "C" gs_status gs_forward_noalloc(gs_problem* p, const void* x, gs_dtype d
     }
     GS_CUDA(launch_loss_reduce(part, c.bpad, p->f_iptr, p->f_list, p->inst_empty, p->h.n_inst, B, loss, s),
             "loss reduce launch");
+    return GS_OK;
+}
+
+// =============================================================================================
+// Straight-through Gumbel training (Eq. 3 with noise, Eq. 4 in the forward pass).
+namespace {
+gs_status st_common(gs_problem* p, int32_t B, int64_t ldB) {
+    if (!p) return fail(GS_ERR_INVALID_ARG, "null problem");
+    gs_status st;
+    if ((st = check_batch(p, kF32, B, ldB)) != GS_OK) return st;
+    return GS_OK;
+}
+}  // namespace
+
+gs_status gs_st_noise(gs_problem* p, uint64_t seed, int64_t step, float* noise, int32_t B, int64_t ldB,
+                      gs_stream stream) {
+    gs_status st;
+    if ((st = st_common(p, B, ldB)) != GS_OK) return st;
+    const bool any = p->h.n > 0 && B > 0;
+    if ((st = need_ptr(noise, "noise", any)) != GS_OK) return st;
+    if (step < 0) return fail(GS_ERR_INVALID_ARG, "step must be >= 0");
+    if ((st = check_device(p)) != GS_OK) return st;
+    if (!any) return GS_OK;
+    GS_CUDA(launch_st_noise(seed, step, noise, p->h.n, B, ldB, static_cast<cudaStream_t>(stream)), "noise launch");
+    return GS_OK;
+}
+
+gs_status gs_st_sample(gs_problem* p, const float* delta, const float* noise, uint64_t seed, int64_t step, int32_t B,
+                       int64_t ldB, uint64_t* bits, gs_stream stream) {
+    gs_status st;
+    if ((st = st_common(p, B, ldB)) != GS_OK) return st;
+    const bool any = p->h.n > 0 && B > 0;
+    if ((st = need_ptr(delta, "delta", any)) != GS_OK || (st = need_ptr(noise, "noise", false)) != GS_OK ||
+        (st = need_ptr(bits, "bits", any)) != GS_OK)
+        return st;
+    if (step < 0) return fail(GS_ERR_INVALID_ARG, "step must be >= 0");
+    if ((st = check_device(p)) != GS_OK) return st;
+    if (!any) return GS_OK;
+    GS_CUDA(launch_st_sample(delta, noise, seed, step, reinterpret_cast<uint32_t*>(bits), p->h.n, B, ldB,
+                             2 * nwords(B), static_cast<cudaStream_t>(stream)),
+            "sample launch");
+    return GS_OK;
+}
+
+gs_status gs_st_step(gs_problem* p, float* delta, float* m, float* v, const uint64_t* bits_in, uint64_t* bits_out,
+                     const float* noise, const float* noise_next, float* noise_next_out, uint64_t seed, int64_t step,
+                     int32_t B, int64_t ldB, const gs_adam* adam, gs_stream stream) {
+    gs_status st;
+    if ((st = st_common(p, B, ldB)) != GS_OK) return st;
+    if (step < 1) return fail(GS_ERR_INVALID_ARG, "step must be >= 1");
+    gs_adam a;
+    gs_adam_default(&a);
+    if (adam) a = *adam;
+    if (!(a.tau > 0.0) || !(a.lr >= 0.0) || !(a.eps >= 0.0) || !(a.beta1 >= 0.0 && a.beta1 < 1.0) ||
+        !(a.beta2 >= 0.0 && a.beta2 < 1.0))
+        return fail(GS_ERR_INVALID_ARG, "Adam hyper-parameters out of range");
+    const bool any = p->h.n > 0 && B > 0;
+    if ((st = need_ptr(delta, "delta", any)) != GS_OK || (st = need_ptr(m, "m", any)) != GS_OK ||
+        (st = need_ptr(v, "v", any)) != GS_OK || (st = need_ptr(bits_in, "bits_in", any)) != GS_OK ||
+        (st = need_ptr(bits_out, "bits_out", any)) != GS_OK || (st = need_ptr(noise, "noise", false)) != GS_OK ||
+        (st = need_ptr(noise_next, "noise_next", false)) != GS_OK ||
+        (st = need_ptr(noise_next_out, "noise_next_out", false)) != GS_OK)
+        return st;
+    if (noise_next && noise_next_out)
+        return fail(GS_ERR_INVALID_ARG, "noise_next_out is only written when noise_next is NULL (generated)");
+    if (noise_next_out && (noise_next_out == noise || noise_next_out == delta || noise_next_out == m || noise_next_out == v))
+        return fail(GS_ERR_INVALID_ARG, "noise_next_out must not alias noise, delta, m or v");
+    if (any && static_cast<const void*>(bits_in) == static_cast<const void*>(bits_out))
+        return fail(GS_ERR_INVALID_ARG, "bits_out must not alias bits_in");
+    if ((st = check_device(p)) != GS_OK) return st;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (!any) return GS_OK;
+    if ((st = ensure_st_ws(p, B, s)) != GS_OK) return st;
+    const StChunking c = st_chunking(B);
+    StParams sp{};
+    sp.items = p->vitems;
+    sp.n_items = p->n_vitems;
+    sp.n_chunks = c.n_chunks;
+    sp.B = B;
+    sp.nw32 = c.nw32;
+    sp.ldB = ldB;
+    sp.codes = p->vcodes;
+    sp.recs = p->vrecs;
+    sp.vtab = p->vtab;
+    sp.bits_in = reinterpret_cast<const uint32_t*>(bits_in);
+    sp.bits_out = reinterpret_cast<uint32_t*>(bits_out);
+    sp.delta = delta;
+    sp.m = m;
+    sp.v = v;
+    sp.noise = noise;
+    sp.noise_next = noise_next;
+    sp.noise_out = noise_next_out;
+    sp.seed = seed;
+    sp.step = step;
+    sp.adam = adam_consts(a, step);
+    sp.split_part = p->split;
+    sp.bpad = c.bpad;
+    sp.split_cnt = p->ctl + 4;
+    sp.head = p->ctl;
+    sp.status = p->status;
+    GS_CUDA(cudaMemsetAsync(p->ctl, 0, sizeof(int32_t) * (4 + static_cast<size_t>(p->h.n_split) * c.n_chunks), s),
+            "memset counters");
+    const int64_t total = static_cast<int64_t>(sp.n_items) * c.n_chunks;
+    if (total > 0) {
+        const int grid = static_cast<int>(std::min<int64_t>(grid_st_pass(c.lw), total));
+        GS_CUDA(launch_st_pass(sp, c.lw, grid, s), "straight-through pass launch");
+    }
     return GS_OK;
 }

@@ -145,6 +145,40 @@ struct VarParams {
     int32_t* status;
 };
 
+// Straight-through Gumbel pass (gs_st_step, Eq. 3-4 with noise): each lane owns one 32-bit word
+// of the bit-packed hard assignment (32 candidates); LW lanes cover a chunk of LW words and the
+// G = 32 / LW lane groups split each variable's occurrences. The integer gradient at the hard
+// point is kept as a signed bit-sliced counter (kStPlanes bit planes, one bit per candidate).
+constexpr int kStPlanes = 10;   // two's complement, |count| <= kVarCodes < 2^9 per tile part
+
+struct StParams {
+    const VarItem* items;
+    int32_t n_items;
+    int32_t n_chunks;        // chunks of LW 32-bit words
+    int32_t B;
+    int32_t nw32;            // 32-bit words per bits row (2 * ceil(B / 64))
+    int64_t ldB;
+    const uint32_t* codes;
+    const uint16_t* recs;
+    const uint32_t* vtab;
+    const uint32_t* bits_in;     // [n][nw32] hard assignment of this step
+    uint32_t* bits_out;          // [n][nw32] hard assignment of the next step
+    float* delta;
+    float* m;
+    float* v;
+    const float* noise;          // [n][ldB] logistic noise of this step, or null: generated
+    const float* noise_next;     // [n][ldB] noise of the next step, or null: generated
+    float* noise_out;            // [n][ldB] receives the generated next-step noise, or null
+    uint64_t seed;
+    int64_t step;
+    AdamK adam;
+    float* split_part;           // [split rows][bpad] partial integer gradients
+    int32_t bpad;                // n_chunks * LW * 32
+    int32_t* split_cnt;          // [n_split][n_chunks]
+    int32_t* head;
+    int32_t* status;
+};
+
 struct FwdParams {
     const FwdItem* items;
     int32_t n_items;
@@ -197,6 +231,12 @@ cudaError_t launch_loss_reduce2(const float* part, int32_t bpad, const int32_t* 
 cudaError_t launch_count_reduce(const uint16_t* part16, int32_t bpad16, const int32_t* iptr, const int32_t* items,
                                 const int64_t* n_empty, int32_t n_inst, int32_t B, int32_t n_seg, int32_t* stage,
                                 int32_t* unsat, int32_t* best, cudaStream_t s);
+cudaError_t launch_st_pass(const StParams& p, int lw, int grid, cudaStream_t s);
+int grid_st_pass(int lw);
+cudaError_t launch_st_noise(uint64_t seed, int64_t step, float* noise, int64_t n, int32_t B, int64_t ldB,
+                            cudaStream_t s);
+cudaError_t launch_st_sample(const float* delta, const float* noise, uint64_t seed, int64_t step, uint32_t* bits32,
+                             int64_t n, int32_t B, int64_t ldB, int32_t nw32, cudaStream_t s);
 cudaError_t launch_relax(const float* delta, void* x, int dtype, int64_t n, int32_t B, int64_t ldB,
                          float inv_tau, cudaStream_t s);
 cudaError_t launch_round(const float* delta, uint32_t* bits32, int64_t n, int32_t B, int64_t ldB,

@@ -5,6 +5,9 @@ keeps only the relaxed values x (nothing per literal) and its backward recompute
 products (Sec. "Differentiable SAT Formulation": forward of Eq. 2 + Eq. 5, back-propagation
 through them).
 
+``STEngine`` runs the paper's own training forward instead: straight-through Gumbel-softmax
+(Eq. 3 with noise, Eq. 4 in the forward pass), whose forward is the bit-packed hard assignment.
+
 ``Engine`` owns one batch of B candidates of a problem: the float32 logit differences delta,
 the Adam moments, two ping-pong buffers of relaxed values x = sigma(delta / tau) in the storage
 dtype, the bit-packed rounded assignments and the per-candidate results. One ``step()`` is the
@@ -145,3 +148,88 @@ class Engine:
         """Rounded assignment of candidate b as 0/1 bytes (host)."""
         words = self.bits[:, b // 64].cpu().numpy().view(np.uint64)
         return ((words >> np.uint64(b % 64)) & np.uint64(1)).astype(np.uint8)[: self.n]
+
+
+class STEngine:
+    """Straight-through Gumbel training of one batch of B candidates (Eq. 3 with noise, Eq. 4 in
+    the forward pass): step t evaluates the loss at the hard assignment x_hat_t = [delta + l_t > 0]
+    (exact unsatisfied-clause counts), takes the integer gradient there through the soft chain
+    y (1 - y) / tau, applies Adam and draws x_hat_{t+1}. The noise l is generated inside the
+    kernels from (noise_seed, step). With ``noise_ring`` (default) each step also stores the next
+    step's noise, which the next step reads instead of drawing it again (two [n, B] float32
+    buffers); without it nothing per candidate is stored besides two bit-packed assignments."""
+
+    def __init__(self, prob: _abi.Problem, B: int, adam: Optional[dict] = None, seed: int = 0, noise_seed: int = 1,
+                 delta0: Optional[np.ndarray] = None, device="cuda", noise_ring: bool = True):
+        self.prob = prob
+        self.B = int(B)
+        self.device = torch.device(device)
+        self.adam = _abi._adam(adam) if adam is not None else None
+        self.noise_seed = int(noise_seed)
+        n = prob.n_vars
+        self.n = n
+        self.delta = candidates(n, B, torch.float32, device)
+        self.m = candidates(n, B, torch.float32, device)
+        self.v = candidates(n, B, torch.float32, device)
+        self.nwd = (self.B + 63) // 64
+        self.bits = [torch.zeros((max(n, 1), self.nwd), dtype=torch.int64, device=device) for _ in range(2)]
+        self.unsat = torch.zeros((prob.n_inst, B), dtype=torch.int32, device=device)
+        self.best = torch.zeros(prob.n_inst, dtype=torch.int32, device=device)
+        self.noise = [candidates(n, B, torch.float32, device) for _ in range(2)] if noise_ring else None
+        _abi.gs_reserve(prob, B, _abi.GS_F32)
+        self.reset(seed, delta0)
+
+    def reset(self, seed: int = 0, delta0: Optional[np.ndarray] = None) -> None:
+        if delta0 is None:
+            delta0 = synth.init_delta(self.n, self.B, seed)
+        d = torch.from_numpy(np.ascontiguousarray(delta0[:, :self.B], dtype=np.float32))
+        self.delta.copy_(d.to(self.device))
+        self.m.zero_()
+        self.v.zero_()
+        self.t = 0
+        self.cur = 0
+        if self.noise is not None:
+            _abi.gs_st_noise(self.prob, self.noise_seed, 1, self.noise[0])
+        _abi.gs_st_sample(self.prob, self.delta, self.bits[0], seed=self.noise_seed, step=1,
+                          noise=self.noise[0] if self.noise is not None else None)
+
+    @property
+    def bits_cur(self) -> torch.Tensor:
+        """Hard assignment x_hat of the next step to run."""
+        return self.bits[self.cur]
+
+    def step(self, check: bool = True) -> None:
+        """One training step (asynchronous on the current stream); with check, unsat / best hold
+        the loss of this step's forward (the unsatisfied clauses of x_hat_t)."""
+        self.t += 1
+        if check:
+            _abi.gs_check_bits(self.prob, self.bits[self.cur], self.B, self.unsat, self.best)
+        ring = self.noise
+        _abi.gs_st_step(self.prob, self.delta, self.m, self.v, self.bits[self.cur], self.bits[self.cur ^ 1],
+                        self.t, seed=self.noise_seed, adam=self.adam,
+                        noise=ring[self.cur] if ring is not None else None,
+                        noise_next_out=ring[self.cur ^ 1] if ring is not None else None)
+        self.cur ^= 1
+
+    def capture(self, steps: int, check: bool = True) -> torch.cuda.CUDAGraph:
+        if steps % 2:
+            raise ValueError("capture an even number of steps so the ping-pong buffers line up")
+        g = torch.cuda.CUDAGraph()
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s):
+            with torch.cuda.graph(g, stream=s):
+                for _ in range(steps):
+                    self.step(check)
+        torch.cuda.current_stream().wait_stream(s)
+        return g
+
+    def run(self, steps: int, graph: bool = True, check: bool = True) -> None:
+        if graph and steps >= 2:
+            even = steps - (steps % 2)
+            self.capture(even, check).replay()
+            for _ in range(steps - even):
+                self.step(check)
+        else:
+            for _ in range(steps):
+                self.step(check)

@@ -49,12 +49,16 @@ def assert_grad(g_gpu, g_ref, scale, what="grad"):
         what, bad.sum(), bad.size, (err / tol).max(), np.argwhere(bad)[:3].tolist())
 
 
-def adam_tolerances(d0, m0, v0, g_ref, scale, t, lr=1.0, b1=0.9, b2=0.999, eps=1e-8, tau=1.0, g_rel=None):
+def adam_tolerances(d0, m0, v0, g_ref, scale, t, lr=1.0, b1=0.9, b2=0.999, eps=1e-8, tau=1.0, g_rel=None, z=None,
+                    z_err=None):
     """Element-wise bounds on |out_gpu - out_oracle| for delta', m', v' after one Adam step,
     propagated from (i) the gradient error bound (1e-5 * max(|g|, A), or g_rel * |g| when the
-    gradient is an exact input) and (ii) a few float32 roundings in each operation."""
+    gradient is an exact input) and (ii) a few float32 roundings in each operation. The chain
+    factor is taken at z = delta / tau, or at the given z (the straight-through form passes
+    (delta + noise) / tau, whose float32 rounding z_err moves the chain factor y (1 - y) by
+    z_err |1 - 2y| relative)."""
     d0, m0, v0, g = (np.asarray(a, dtype=np.float64) for a in (d0, m0, v0, g_ref))
-    z = d0 / tau
+    z = d0 / tau if z is None else np.asarray(z, dtype=np.float64) / tau
     sp, sn = 1.0 / (1.0 + np.exp(-z)), 1.0 / (1.0 + np.exp(z))
     chain = sp * sn / tau
     if g_rel is None:
@@ -63,6 +67,8 @@ def adam_tolerances(d0, m0, v0, g_ref, scale, t, lr=1.0, b1=0.9, b2=0.999, eps=1
         eg = g_rel * np.abs(g)
     gd = g * chain
     egd = eg * chain + 8 * U32 * np.abs(gd)                     # chain factor: expf, divide, products
+    if z_err is not None:
+        egd = egd + np.abs(gd) * np.asarray(z_err, dtype=np.float64) * np.abs(1.0 - 2.0 * sp)
     m1 = b1 * m0 + (1 - b1) * gd
     v1 = b2 * v0 + (1 - b2) * gd * gd
     em = (1 - b1) * egd + 4 * U32 * (np.abs(m1) + b1 * np.abs(m0))
