@@ -45,9 +45,9 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle sample")
     ap.add_argument("--no-autotune", action="store_true", help="skip gs_autotune (use defaults / --var-* flags)")
-    ap.add_argument("--legs", default="st,precision,plain,structured",
+    ap.add_argument("--legs", default="st,precision,tseitin,plain,structured",
                     help="extra single-GPU measurements added to the line under 'legs' (comma list of st, precision, "
-                         "plain, structured, batching; 'none' for none)")
+                         "tseitin, plain, structured, batching; 'none' for none)")
     ap.add_argument("--leg-steps", type=int, default=50, help="timed steps of each extra leg")
     ap.add_argument("--var-lanes", type=int, default=0, help="cap on lanes per candidate chunk (gs_set_tuning)")
     ap.add_argument("--var-gather", type=int, default=0, help="0: automatic, 1: register loads, 2: TMA gather4 ring (gs_set_tuning)")
@@ -358,6 +358,32 @@ def leg_batching(torch, args, peak):
     return out
 
 
+def leg_tseitin(torch, args, peak):
+    """The paper's formulation vs the native one on the mixed-width power-law formula (FP32,
+    B = 256): the width-3 chain normalisation of Eq. 6-8 (gs_tseitin3: more variables and
+    clauses, every clause of width 3) against the formula with its own clause widths."""
+    from paper_2603_28796_b300 import _abi
+    from paper_2603_28796_b300.engine import Engine
+
+    cnf, B, _, desc = workload_setup("precision")
+    n3, cp3, lits3 = _abi.gs_tseitin3(cnf.n_vars, cnf.clause_ptr, cnf.lits)
+    out = {"workload": desc.replace("BF16 storage vs FP32", "FP32") + "; native widths vs width-3 chains (Eq. 6-8)",
+           "B": B}
+    for name, (n, cp, lits) in (("native", (cnf.n_vars, cnf.clause_ptr, cnf.lits)), ("width3", (n3, cp3, lits3))):
+        prob = _abi.gs_load_cnf(n, cp, lits)
+        tuning = _abi.gs_autotune(prob, B, "f32")
+        eng = Engine(prob, B, "f32", seed=13)
+        ms, step_ms = _timed_steps(torch, eng, args.leg_steps, args.warmup)
+        nnz = int(cp[-1])
+        out[name] = {"n": n, "m": int(cp.size - 1), "nnz": nnz, "ms_per_step": ms, "steps_per_s": 1000.0 / ms,
+                     "evals_per_s": nnz * B / (ms / 1000.0), "gs_step_ms": step_ms, "tuning": tuning}
+        del eng
+        prob.close()
+        torch.cuda.empty_cache()
+    out["native_speedup"] = out["width3"]["ms_per_step"] / out["native"]["ms_per_step"]
+    return out
+
+
 def leg_st(torch, args, peak):
     """The paper's own training forward on the differentiation workload: straight-through Gumbel
     (hard assignment in the forward pass, soft chain in the backward pass, noise drawn in the
@@ -415,6 +441,8 @@ def run_legs(torch, args, peak):
                 legs[name] = leg_structured(torch, args, peak)
             elif name == "st":
                 legs[name] = leg_st(torch, args, peak)
+            elif name == "tseitin":
+                legs[name] = leg_tseitin(torch, args, peak)
             elif name == "batching":
                 legs[name] = leg_batching(torch, args, peak)
             else:

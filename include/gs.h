@@ -134,6 +134,20 @@ gs_status gs_load_dimacs(const char* path, gs_stream stream, gs_problem** out);
 gs_status gs_inspect_cnf(int64_t n_vars, int64_t n_clauses, const int64_t* clause_ptr, const int32_t* lits,
                          gs_info* out);
 
+/*
+ * gs_tseitin3 - the paper's width normalisation (Sec. "Clause Normalization for Vectorization",
+ * Eq. 6-8, host only, no device work): every clause of u > 3 literals becomes the chain
+ *   (l1 v l2 v f1) (-f1 v l3 v f2) ... (-f_{u-3} v l_{u-1} v l_u)
+ * over fresh variables f numbered n_vars + 1, n_vars + 2, ... in clause order; a clause of 1 or
+ * 2 literals repeats its last literal to width 3 (the appendix's (-x1 v x3 v x3)); width 3 is
+ * kept and an empty clause stays empty. The result is equisatisfiable with the input and its
+ * first n_vars variables are the input's. Call once with clause_ptr_out = lits_out = NULL to get
+ * *n_out, *m_out, *nnz_out, then with host buffers of m_out + 1 and nnz_out entries.
+ * Errors: as gs_inspect_cnf.
+ */
+gs_status gs_tseitin3(int64_t n_vars, int64_t n_clauses, const int64_t* clause_ptr, const int32_t* lits,
+                      int64_t* n_out, int64_t* m_out, int64_t* nnz_out, int64_t* clause_ptr_out, int32_t* lits_out);
+
 /* gs_info_get - statistics of a loaded problem. GS_ERR_INVALID_ARG on null arguments. */
 gs_status gs_info_get(const gs_problem* prob, gs_info* out);
 

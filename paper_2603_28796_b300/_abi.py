@@ -28,7 +28,7 @@ STATUS_NAMES = {
 EXPORTED = (
     "gs_adam_default", "gs_load_cnf", "gs_load_batch", "gs_load_dimacs", "gs_inspect_cnf", "gs_info_get",
     "gs_set_tuning", "gs_get_tuning", "gs_autotune", "gs_reserve", "gs_relax", "gs_forward", "gs_forward_noalloc", "gs_backward", "gs_step", "gs_round_check", "gs_check_bits",
-    "gs_st_noise", "gs_st_sample", "gs_st_step",
+    "gs_st_noise", "gs_st_sample", "gs_st_step", "gs_tseitin3",
     "gs_wait_selftest", "gs_sync_status", "gs_free", "gs_status_str", "gs_last_error",
 )
 
@@ -100,6 +100,7 @@ def lib():
                                        ctypes.POINTER(GsAdam), vp, vp, vp]),
             "gs_round_check": (ctypes.c_int, [vp, vp, i32, i64, vp, vp, vp, vp]),
             "gs_check_bits": (ctypes.c_int, [vp, vp, i32, vp, vp, vp]),
+            "gs_tseitin3": (ctypes.c_int, [i64, i64, vp, vp, vp, vp, vp, vp, vp]),
             "gs_st_noise": (ctypes.c_int, [vp, ctypes.c_uint64, i64, vp, i32, i64, vp]),
             "gs_st_sample": (ctypes.c_int, [vp, vp, vp, ctypes.c_uint64, i64, i32, i64, vp, vp]),
             "gs_st_step": (ctypes.c_int, [vp, vp, vp, vp, vp, vp, vp, vp, vp, ctypes.c_uint64, i64, i32, i64,
@@ -255,6 +256,20 @@ def gs_inspect_cnf(n_vars: int, clause_ptr, lits) -> dict:
     _check(lib().gs_inspect_cnf(int(n_vars), cp.size - 1, _np_ptr(cp), _np_ptr(lt) if lt.size else None,
                                 ctypes.byref(gi)), "gs_inspect_cnf")
     return gi.as_dict()
+
+
+def gs_tseitin3(n_vars: int, clause_ptr, lits):
+    """Width-3 chain normalisation (Eq. 6-8) on the host: returns (n', clause_ptr', lits'); the
+    first n_vars variables are the input's, the rest are the chains' fresh variables."""
+    cp, lt = _csr(clause_ptr, lits)
+    n2, m2, z2 = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+    args = (int(n_vars), cp.size - 1, _np_ptr(cp), _np_ptr(lt) if lt.size else None)
+    _check(lib().gs_tseitin3(*args, ctypes.byref(n2), ctypes.byref(m2), ctypes.byref(z2), None, None), "gs_tseitin3")
+    cp2 = np.zeros(m2.value + 1, dtype=np.int64)
+    lt2 = np.zeros(max(z2.value, 1), dtype=np.int32)
+    _check(lib().gs_tseitin3(*args, ctypes.byref(n2), ctypes.byref(m2), ctypes.byref(z2), _np_ptr(cp2), _np_ptr(lt2)),
+           "gs_tseitin3")
+    return int(n2.value), cp2, lt2[: z2.value]
 
 
 def gs_info_get(prob: Problem) -> dict:

@@ -1075,3 +1075,11 @@ gs_status gs_st_step(gs_problem* p, float* delta, float* m, float* v, const uint
     }
     return GS_OK;
 }
+
+gs_status gs_tseitin3(int64_t n_vars, int64_t n_clauses, const int64_t* clause_ptr, const int32_t* lits,
+                      int64_t* n_out, int64_t* m_out, int64_t* nnz_out, int64_t* clause_ptr_out, int32_t* lits_out) {
+    std::string err;
+    const gs_status st =
+        tseitin3(n_vars, n_clauses, clause_ptr, lits, n_out, m_out, nnz_out, clause_ptr_out, lits_out, &err);
+    return st == GS_OK ? GS_OK : fail(st, err);
+}

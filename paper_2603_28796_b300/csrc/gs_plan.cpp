@@ -476,4 +476,69 @@ gs_status build_plan(int32_t n_inst, const int64_t* n_vars, const int64_t* n_cla
     }
 }
 
+gs_status tseitin3(int64_t n, int64_t m, const int64_t* clause_ptr, const int32_t* lits, int64_t* n_out,
+                   int64_t* m_out, int64_t* nnz_out, int64_t* cp_out, int32_t* lits_out, std::string* err) {
+    if (!n_out || !m_out || !nnz_out) return *err = "null size output", GS_ERR_INVALID_ARG;
+    HostPlan P;
+    gs_status st;
+    try {
+        st = validate(1, &n, &m, clause_ptr, lits, P, err);
+    } catch (const std::bad_alloc&) {
+        return *err = "host allocation failed", GS_ERR_OOM;
+    }
+    if (st != GS_OK) return st;
+    int64_t n2 = n, m2 = 0, nnz2 = 0;
+    for (int64_t t = 0; t < m; ++t) {
+        const int64_t u = clause_ptr[t + 1] - clause_ptr[t];
+        if (u == 0) {
+            m2 += 1;
+        } else if (u <= 3) {
+            m2 += 1;
+            nnz2 += 3;
+        } else {
+            m2 += u - 2;
+            nnz2 += 3 * (u - 2);
+            n2 += u - 3;
+        }
+    }
+    if (n2 > kMaxVars) return *err = "normalised formula has too many variables (limit 2^28 - 2)", GS_ERR_UNSUPPORTED;
+    *n_out = n2;
+    *m_out = m2;
+    *nnz_out = nnz2;
+    if (!cp_out && !lits_out) return GS_OK;
+    if (!cp_out || !lits_out) return *err = "cp_out and lits_out must both be given", GS_ERR_INVALID_ARG;
+    int64_t c = 0, j = 0;
+    int32_t fresh = static_cast<int32_t>(n);   // last variable number used
+    cp_out[0] = 0;
+    auto emit = [&](int32_t a, int32_t b, int32_t d) {
+        lits_out[j++] = a;
+        lits_out[j++] = b;
+        lits_out[j++] = d;
+        cp_out[++c] = j;
+    };
+    for (int64_t t = 0; t < m; ++t) {
+        const int32_t* l = lits + clause_ptr[t];
+        const int64_t u = clause_ptr[t + 1] - clause_ptr[t];
+        if (u == 0) {
+            cp_out[++c] = j;
+        } else if (u == 1) {
+            emit(l[0], l[0], l[0]);
+        } else if (u == 2) {
+            emit(l[0], l[1], l[1]);
+        } else if (u == 3) {
+            emit(l[0], l[1], l[2]);
+        } else {
+            int32_t f = ++fresh;
+            emit(l[0], l[1], f);
+            for (int64_t i = 2; i < u - 2; ++i) {
+                const int32_t g = ++fresh;
+                emit(-f, l[i], g);
+                f = g;
+            }
+            emit(-f, l[u - 2], l[u - 1]);
+        }
+    }
+    return GS_OK;
+}
+
 }  // namespace gs

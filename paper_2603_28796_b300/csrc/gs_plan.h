@@ -36,4 +36,12 @@ struct HostPlan {
 gs_status build_plan(int32_t n_inst, const int64_t* n_vars, const int64_t* n_clauses, const int64_t* clause_ptr,
                      const int32_t* lits, HostPlan& P, std::string* err);
 
+// Chain (Tseitin) normalisation to width 3 (Sec. "Clause Normalization for Vectorization", Eq. 6-8):
+// a clause of u > 3 literals becomes (l1 v l2 v f1) (-f1 v l3 v f2) ... (-f_{u-3} v l_{u-1} v l_u)
+// with fresh variables f numbered after the formula's own (in clause order); a clause of u = 1 or
+// 2 literals repeats its last literal up to 3; u = 3 is kept; an empty clause stays empty.
+// With cp_out / lits_out NULL only the sizes are returned. Errors as build_plan's validation.
+gs_status tseitin3(int64_t n, int64_t m, const int64_t* clause_ptr, const int32_t* lits, int64_t* n_out,
+                   int64_t* m_out, int64_t* nnz_out, int64_t* cp_out, int32_t* lits_out, std::string* err);
+
 }  // namespace gs
