@@ -353,6 +353,37 @@ gs_status gs_st_step(gs_problem* prob, float* delta, float* m, float* v, const u
                      int32_t B, int64_t ldB, const gs_adam* adam, gs_stream stream);
 
 /*
+ * Candidate pool (Sec. "Partial Assignment Extraction for SAT Instances", the pool of Eq. 9) and
+ * branching variables (Sec. "Guided Branching for UNSAT Instances"), from one trained candidate's
+ * logits delta (the selected batch): row v of it is delta[v * stride] (a column of a [n][ldB]
+ * array: pass delta + b_sel and stride ldB). Only rows 0 .. n_rows - 1 take part (the formula's
+ * own variables when fresh chain variables follow them, Eq. 6-8).
+ * Confidence of variable v in a sample is max_j y_j = sigma(|delta_v + l| / tau); it is ranked by
+ * |delta_v + l| (the same order; float32 sigma would tie everything beyond |z| = 17), ties to the
+ * lower row, so the result does not depend on tau.
+ *
+ * gs_pool_sample - N samples x^(k) = [delta + l^(k) > 0] with independent logistic noise and, for
+ * each, the S rows of highest confidence.
+ *   noise  device float [n_rows][ldN] (ldN >= N) holding l, or NULL: drawn from the generator of
+ *          gs_st_noise with this seed and step 0, sample k in the place of candidate k.
+ *   bits   device uint64 [n_rows][ceil(N/64)] receiving the samples (bits >= N zero), or NULL.
+ *   sel    device int32 [N][S] receiving each sample's selected rows, ascending.
+ *   1 <= S <= min(n_rows, 8192); 1 <= N <= 2^20. Uses a library workspace of 256 KiB per sample.
+ * gs_branch_vars - the d rows of lowest confidence sigma(|delta_v| / tau), i.e. smallest |delta_v|
+ *   (ties to the lower row), ascending in vars (device int32 [d]); 1 <= d <= min(n_rows, 8192).
+ * Both are asynchronous on the stream. The unit clauses (x_v if the sample's bit is 1, else
+ * not x_v) for each selected row, or the 2^d sign patterns of the branching rows, are added to
+ * the formula by the host (a DIMACS writer is in the Python package).
+ * Errors: GS_ERR_INVALID_ARG, GS_ERR_UNSUPPORTED (S or d beyond 8192), GS_ERR_OOM, GS_ERR_STATE,
+ * GS_ERR_CUDA.
+ */
+gs_status gs_pool_sample(gs_problem* prob, const float* delta, int64_t stride, int32_t n_rows, const float* noise,
+                         int64_t ldN, uint64_t seed, int32_t N, int32_t S, uint64_t* bits, int32_t* sel,
+                         gs_stream stream);
+gs_status gs_branch_vars(gs_problem* prob, const float* delta, int64_t stride, int32_t n_rows, int32_t d,
+                         int32_t* vars, gs_stream stream);
+
+/*
  * gs_wait_selftest - exercises the device-side failure path: one warp waits on a barrier phase
  * that nothing completes, gives up after limit_us microseconds (1..1e7) and records
  * GS_ERR_TIMEOUT in the problem's sticky status, exactly as a stalled tile copy would. No

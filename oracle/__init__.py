@@ -204,3 +204,34 @@ def st_step(n_vars, clause_ptr, lits, delta, m, v, noise, noise_next, t, lr=1.0,
     d1, m1, v1 = st_adam(d, m, v, g, noise, t, lr, beta1, beta2, eps, tau)
     x_next, unsat_next, _ = round_check(n_vars, clause_ptr, lits, d1 + _f64(noise_next))
     return dict(x_hat=x_hat, unsat=unsat, grad=g, delta=d1, m=m1, v=v1, x_hat_next=x_next, unsat_next=unsat_next)
+
+
+# ---------------------------------------------------------------------------------------------
+# Candidate pool (Sec. "Partial Assignment Extraction for SAT Instances", Eq. 9) and branching
+# variables (Sec. "Guided Branching for UNSAT Instances"), written as plain sorts.
+def pool_select(delta_col, noise, S):
+    """Samples and selections around one candidate.
+
+    delta_col float32 [n] (the candidate's logits), noise float32 [n, N] (one logistic draw per
+    variable and sample). z = delta + l in float32 (one rounding, as the kernels add), sample
+    x^(k) = [z > 0] (Eq. 4 on the noisy logits), confidence c = sigma(|z| / tau) = max_j y_j,
+    ranked by |z| (sigma is increasing), ties to the lower row; the S highest per sample.
+    Returns (x uint8 [N, n], sel int32 [N, S], rows ascending)."""
+    d = np.asarray(delta_col, dtype=np.float32).reshape(-1, 1)
+    z = (d + np.asarray(noise, dtype=np.float32)).astype(np.float32)
+    n, N = z.shape
+    x = (z > 0).astype(np.uint8).T
+    rows = np.arange(n)
+    sel = np.empty((N, int(S)), dtype=np.int32)
+    for k in range(N):
+        order = np.lexsort((rows, -np.abs(z[:, k]).astype(np.float64)))
+        sel[k] = np.sort(order[: int(S)])
+    return x, sel
+
+
+def branch_select(delta_col, d):
+    """The d variables of lowest confidence sigma(|delta| / tau), i.e. smallest |delta|, ties to the
+    lower row; rows ascending."""
+    a = np.abs(np.asarray(delta_col, dtype=np.float32)).astype(np.float64)
+    order = np.lexsort((np.arange(a.size), a))
+    return np.sort(order[: int(d)]).astype(np.int32)

@@ -17,7 +17,8 @@ _ABI_NAMES = (
     "GS_BF16", "GS_F16", "GS_F32", "GSError", "Problem", "gs_adam_default", "gs_backward", "gs_check_bits",
     "gs_forward", "gs_free", "gs_info_get", "gs_inspect_cnf", "gs_last_error", "gs_load_batch", "gs_load_cnf",
     "gs_load_dimacs", "gs_relax", "gs_reserve", "gs_set_tuning", "gs_get_tuning", "gs_autotune", "gs_forward_noalloc", "gs_round_check", "gs_status_str", "gs_step", "gs_sync_status", "gs_wait_selftest", "gs_st_noise",
-    "gs_st_sample", "gs_st_step", "gs_tseitin3",
+    "gs_st_sample", "gs_st_step", "gs_tseitin3", "gs_pool_sample",
+    "gs_branch_vars",
 )
 
 

@@ -28,7 +28,7 @@ STATUS_NAMES = {
 EXPORTED = (
     "gs_adam_default", "gs_load_cnf", "gs_load_batch", "gs_load_dimacs", "gs_inspect_cnf", "gs_info_get",
     "gs_set_tuning", "gs_get_tuning", "gs_autotune", "gs_reserve", "gs_relax", "gs_forward", "gs_forward_noalloc", "gs_backward", "gs_step", "gs_round_check", "gs_check_bits",
-    "gs_st_noise", "gs_st_sample", "gs_st_step", "gs_tseitin3",
+    "gs_st_noise", "gs_st_sample", "gs_st_step", "gs_tseitin3", "gs_pool_sample", "gs_branch_vars",
     "gs_wait_selftest", "gs_sync_status", "gs_free", "gs_status_str", "gs_last_error",
 )
 
@@ -101,6 +101,8 @@ def lib():
             "gs_round_check": (ctypes.c_int, [vp, vp, i32, i64, vp, vp, vp, vp]),
             "gs_check_bits": (ctypes.c_int, [vp, vp, i32, vp, vp, vp]),
             "gs_tseitin3": (ctypes.c_int, [i64, i64, vp, vp, vp, vp, vp, vp, vp]),
+            "gs_pool_sample": (ctypes.c_int, [vp, vp, i64, i32, vp, i64, ctypes.c_uint64, i32, i32, vp, vp, vp]),
+            "gs_branch_vars": (ctypes.c_int, [vp, vp, i64, i32, i32, vp, vp]),
             "gs_st_noise": (ctypes.c_int, [vp, ctypes.c_uint64, i64, vp, i32, i64, vp]),
             "gs_st_sample": (ctypes.c_int, [vp, vp, vp, ctypes.c_uint64, i64, i32, i64, vp, vp]),
             "gs_st_step": (ctypes.c_int, [vp, vp, vp, vp, vp, vp, vp, vp, vp, ctypes.c_uint64, i64, i32, i64,
@@ -438,6 +440,46 @@ def gs_st_step(prob: Problem, delta, m, v, bits_in, bits_out, step: int, seed: i
     _check(lib().gs_st_step(prob.handle, _ptr(delta), _ptr(m), _ptr(v), _ptr(bits_in), _ptr(bits_out), _ptr(noise),
                             _ptr(noise_next), _ptr(noise_next_out), _seed(seed), int(step), B, ldB,
                             ctypes.byref(a) if a is not None else None, _stream(stream)), "gs_st_step")
+
+
+# ------------------------------------------------------------------------------------------
+# Candidate pool and branching variables.
+def _column(delta, b: int):
+    """(device pointer, stride) of candidate column b of a var-major float32 [n, B] tensor."""
+    if delta.dtype != _torch().float32:
+        raise ValueError("delta must be float32")
+    if not (0 <= b < delta.shape[1]):
+        raise ValueError("candidate index out of range")
+    return delta.data_ptr() + 4 * int(b) * delta.stride(1), delta.stride(0)
+
+
+def gs_pool_sample(prob: Problem, delta, b: int, N: int, S: int, seed: int = 0, n_rows=None, noise=None,
+                   bits=None, stream=None):
+    """N noisy samples around candidate b of delta and each sample's S most confident rows.
+    Returns (bits [n_rows, ceil(N/64)] int64, sel [N, S] int32) on the device."""
+    torch = _torch()
+    ptr, stride = _column(delta, b)
+    nr = prob.n_vars if n_rows is None else int(n_rows)
+    if bits is None:
+        bits = torch.zeros((max(nr, 1), (int(N) + 63) // 64), dtype=torch.int64, device=delta.device)
+    sel = torch.empty((int(N), int(S)), dtype=torch.int32, device=delta.device)
+    ldN = 0
+    if noise is not None:
+        if noise.dtype != torch.float32 or noise.stride(1) != 1 or noise.shape[1] < N:
+            raise ValueError("noise must be float32 [n_rows, >= N] with unit column stride")
+        ldN = noise.stride(0)
+    _check(lib().gs_pool_sample(prob.handle, ptr, stride, nr, _ptr(noise), ldN, _seed(seed), int(N), int(S),
+                                _ptr(bits), _ptr(sel), _stream(stream)), "gs_pool_sample")
+    return bits, sel
+
+
+def gs_branch_vars(prob: Problem, delta, b: int, d: int, n_rows=None, stream=None):
+    """The d rows of candidate b with the smallest |delta| (least confident), ascending."""
+    ptr, stride = _column(delta, b)
+    nr = prob.n_vars if n_rows is None else int(n_rows)
+    out = _torch().empty(int(d), dtype=_torch().int32, device=delta.device)
+    _check(lib().gs_branch_vars(prob.handle, ptr, stride, nr, int(d), _ptr(out), _stream(stream)), "gs_branch_vars")
+    return out
 
 
 def gs_wait_selftest(prob: Problem, limit_us: int = 1000, stream=None) -> None:

@@ -22,8 +22,8 @@ LIB = os.path.join(HERE, "libgaloissat.so")
 SYNTH = os.path.join(HERE, "libgs_synth.so")
 BUILD_DIR = os.path.join(HERE, "_build")
 
-CUDA_SOURCES = ["gs_host.cu", "gs_kernels.cu", "gs_st.cu", "gs_plan.cpp"]
-CUDA_HEADERS = ["gs_internal.h", "gs_plan.h", "gs_device.cuh"]
+CUDA_SOURCES = ["gs_host.cu", "gs_kernels.cu", "gs_st.cu", "gs_pool.cu", "gs_plan.cpp"]
+CUDA_HEADERS = ["gs_internal.h", "gs_plan.h", "gs_device.cuh", "gs_noise.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

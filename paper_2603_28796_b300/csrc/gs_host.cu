@@ -102,6 +102,8 @@ struct gs_problem {
     size_t bits_cap = 0;         // words
     uint16_t* part16 = nullptr;  // per-tile unsat counts
     size_t part16_cap = 0;
+    unsigned char* pool = nullptr;   // candidate-pool selection workspace
+    size_t pool_cap = 0;             // bytes
     double* stage = nullptr;     // stage-1 sums of the tile reductions (double or int32)
     size_t stage_cap = 0;        // doubles
     int sms = 148;
@@ -873,6 +875,7 @@ gs_status gs_sync_status(gs_problem* p) {
     if (h) {
         GS_CUDA(cudaMemset(p->status, 0, sizeof(int32_t)), "clear status");
         if (h & kStatusTimeout) return fail(GS_ERR_TIMEOUT, "a bounded device-side wait timed out");
+        if (h & kStatusSelect) return fail(GS_ERR_STATE, "a pool selection found more rows than its rank");
     }
     return GS_OK;
 }
@@ -883,7 +886,7 @@ void gs_free(gs_problem* p) {
     if (cudaGetDevice(&dev) == cudaSuccess && dev == p->device) cudaDeviceSynchronize();
     void* ptrs[] = {p->fcodes, p->fctab,  p->fitems,     p->vcodes, p->vrecs, p->vtab,  p->vitems,
                     p->f_iptr, p->f_list, p->v_iptr,     p->v_list, p->inst_empty, p->status, p->ctl,
-                    p->part,   p->split,  p->bits,       p->part16, p->stage};
+                    p->part,   p->split,  p->bits,       p->part16, p->stage, p->pool};
     for (void* q : ptrs)
         if (q) cudaFree(q);
     delete p;
@@ -1082,4 +1085,62 @@ gs_status gs_tseitin3(int64_t n_vars, int64_t n_clauses, const int64_t* clause_p
     const gs_status st =
         tseitin3(n_vars, n_clauses, clause_ptr, lits, n_out, m_out, nnz_out, clause_ptr_out, lits_out, &err);
     return st == GS_OK ? GS_OK : fail(st, err);
+}
+
+// =============================================================================================
+// Candidate pool and branching variables (Sec. "Partial Assignment Extraction for SAT Instances",
+// Sec. "Guided Branching for UNSAT Instances").
+namespace {
+gs_status pool_run(gs_problem* p, const float* delta, int64_t stride, int32_t n_rows, const float* noise, int64_t ldN,
+                   uint64_t seed, int32_t N, int32_t S, bool branch, uint64_t* bits, int32_t* sel, cudaStream_t s) {
+    if (stride < 1) return fail(GS_ERR_INVALID_ARG, "stride must be >= 1");
+    if (n_rows < 0 || n_rows > p->h.n) return fail(GS_ERR_INVALID_ARG, "n_rows outside 0..n_vars");
+    if (N < 1 || N > (1 << 20)) return fail(GS_ERR_INVALID_ARG, "N outside 1..2^20");
+    if (S < 1 || S > n_rows) return fail(GS_ERR_INVALID_ARG, "the selection size must be in 1..n_rows");
+    if (S > kPoolMaxS) return fail(GS_ERR_UNSUPPORTED, "selection size beyond 8192 rows per sample");
+    if (!delta || !sel) return fail(GS_ERR_INVALID_ARG, "null delta or selection output");
+    if (noise && ldN < N) return fail(GS_ERR_INVALID_ARG, "ldN < N");
+    gs_status st;
+    if ((st = check_device(p)) != GS_OK) return st;
+    const size_t hist_b = sizeof(uint32_t) * 65536u * static_cast<size_t>(N);
+    const size_t need = hist_b + static_cast<size_t>(N) * (8 + 4 + 4) + 64;
+    if ((st = grow(&p->pool, &p->pool_cap, need, s, capturing(s), "pool selection")) != GS_OK) return st;
+    PoolParams pp{};
+    pp.delta = delta;
+    pp.stride = stride;
+    pp.noise = branch ? nullptr : noise;
+    pp.ldN = ldN;
+    pp.seed = seed;
+    pp.n_rows = n_rows;
+    pp.N = N;
+    pp.S = S;
+    pp.nw32 = 2 * ((N + 63) / 64);
+    pp.branch = branch;
+    pp.bits32 = reinterpret_cast<uint32_t*>(bits);
+    pp.hist = reinterpret_cast<uint32_t*>(p->pool);
+    pp.prefix = reinterpret_cast<unsigned long long*>(p->pool + hist_b);
+    pp.rem = reinterpret_cast<int32_t*>(p->pool + hist_b + 8 * static_cast<size_t>(N));
+    pp.count = pp.rem + N;
+    pp.sel = sel;
+    pp.status = p->status;
+    GS_CUDA(launch_pool_select(pp, s), "pool selection launch");
+    return GS_OK;
+}
+}  // namespace
+
+gs_status gs_pool_sample(gs_problem* p, const float* delta, int64_t stride, int32_t n_rows, const float* noise,
+                         int64_t ldN, uint64_t seed, int32_t N, int32_t S, uint64_t* bits, int32_t* sel,
+                         gs_stream stream) {
+    if (!p) return fail(GS_ERR_INVALID_ARG, "null problem");
+    gs_status st;
+    if ((st = need_ptr(noise, "noise", false)) != GS_OK || (st = need_ptr(bits, "bits", false)) != GS_OK) return st;
+    return pool_run(p, delta, stride, n_rows, noise, ldN, seed, N, S, false, bits, sel,
+                    static_cast<cudaStream_t>(stream));
+}
+
+gs_status gs_branch_vars(gs_problem* p, const float* delta, int64_t stride, int32_t n_rows, int32_t d, int32_t* vars,
+                         gs_stream stream) {
+    if (!p) return fail(GS_ERR_INVALID_ARG, "null problem");
+    return pool_run(p, delta, stride, n_rows, nullptr, 0, 0, 1, d, true, nullptr, vars,
+                    static_cast<cudaStream_t>(stream));
 }

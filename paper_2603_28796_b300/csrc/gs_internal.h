@@ -179,6 +179,29 @@ struct StParams {
     int32_t* status;
 };
 
+// Candidate pool / branching selection (gs_pool_sample, gs_branch_vars).
+constexpr int kPoolMaxS = 8192;   // selected rows per sample (one shared-memory sort per sample)
+
+struct PoolParams {
+    const float* delta;          // the selected candidate's logits: row v at delta[v * stride]
+    int64_t stride;
+    const float* noise;          // [n_rows][ldN] logistic noise of the N samples, or null: generated
+    int64_t ldN;
+    uint64_t seed;
+    int32_t n_rows;              // rows taking part (the formula's own variables)
+    int32_t N;                   // samples
+    int32_t S;                   // rows selected per sample
+    int32_t nw32;                // 32-bit words per bits row (2 * ceil(N / 64))
+    bool branch;                 // keys from |delta| ascending (N = 1), no noise
+    uint32_t* bits32;            // [n_rows][nw32] samples, or null
+    uint32_t* hist;              // [N][65536]
+    unsigned long long* prefix;  // [N] radix prefix (ends as the S-th largest key)
+    int32_t* rem;                // [N] remaining rank
+    int32_t* count;              // [N] rows appended
+    int32_t* sel;                // [N][S] selected rows
+    int32_t* status;
+};
+
 struct FwdParams {
     const FwdItem* items;
     int32_t n_items;
@@ -211,6 +234,7 @@ struct CheckParams {
 
 // Device status bits (sticky until read by gs_sync_status).
 constexpr int32_t kStatusTimeout = 1;
+constexpr int32_t kStatusSelect = 2;   // a selection found more rows than its rank (never expected)
 
 // ---------------------------------------------------------------------------------------------
 // Launchers (gs_kernels.cu). They return cudaGetLastError() of the launch.
@@ -232,6 +256,7 @@ cudaError_t launch_count_reduce(const uint16_t* part16, int32_t bpad16, const in
                                 const int64_t* n_empty, int32_t n_inst, int32_t B, int32_t n_seg, int32_t* stage,
                                 int32_t* unsat, int32_t* best, cudaStream_t s);
 cudaError_t launch_st_pass(const StParams& p, int lw, int grid, cudaStream_t s);
+cudaError_t launch_pool_select(const PoolParams& p, cudaStream_t s);
 int grid_st_pass(int lw);
 cudaError_t launch_st_noise(uint64_t seed, int64_t step, float* noise, int64_t n, int32_t B, int64_t ldB,
                             cudaStream_t s);

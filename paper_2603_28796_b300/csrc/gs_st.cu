@@ -24,30 +24,10 @@
 
 #include "gs_device.cuh"
 #include "gs_internal.h"
+#include "gs_noise.cuh"
 
 namespace gs {
 namespace {
-
-constexpr uint32_t kPhM0 = 0xD2511F53u;   // Philox4x32 round multipliers
-constexpr uint32_t kPhM1 = 0xCD9E8D57u;
-constexpr uint32_t kPhW0 = 0x9E3779B9u;   // Weyl increments of the key
-constexpr uint32_t kPhW1 = 0xBB67AE85u;
-
-__device__ __forceinline__ void philox4x32_10(uint32_t (&x)[4], uint32_t k0, uint32_t k1) {
-#pragma unroll
-    for (int r = 0; r < 10; ++r) {
-        const uint64_t p0 = static_cast<uint64_t>(kPhM0) * x[0];
-        const uint64_t p1 = static_cast<uint64_t>(kPhM1) * x[2];
-        const uint32_t y0 = static_cast<uint32_t>(p1 >> 32) ^ x[1] ^ k0;
-        const uint32_t y2 = static_cast<uint32_t>(p0 >> 32) ^ x[3] ^ k1;
-        x[1] = static_cast<uint32_t>(p1);
-        x[3] = static_cast<uint32_t>(p0);
-        x[0] = y0;
-        x[2] = y2;
-        k0 += kPhW0;
-        k1 += kPhW1;
-    }
-}
 
 // Logistic noise of candidates c0 .. c0 + 7 (c0 a multiple of 8) of batch row `row` at `step`.
 __device__ __forceinline__ void logistic8(uint64_t seed, int64_t step, int64_t row, int c0, float (&l)[8]) {
@@ -59,8 +39,7 @@ __device__ __forceinline__ void logistic8(uint64_t seed, int64_t step, int64_t r
         philox4x32_10(x, k0, k1);
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-            const float u = (static_cast<float>(x[j] >> 9) + 0.5f) * 0x1p-23f;
-            l[4 * h + j] = logf(__fdiv_rn(u, 1.0f - u));
+            l[4 * h + j] = logistic_from_word(x[j]);
         }
     }
 }
