@@ -169,6 +169,10 @@ gs_status gs_reserve(gs_problem* prob, int32_t B, gs_dtype dtype);
  *              0 = automatic (currently per-lane register loads), 1 = per-lane register loads,
  *              2 = TMA tile::gather4 copies into a shared-memory ring when a chunk spans 32
  *              lanes (register loads otherwise).
+ *   loss_mode  how the fused step (gs_step with grad = NULL) produces its loss: 0 = automatic
+ *              (currently 1), 1 = credited inside the variable-major pass at each clause's first
+ *              literal, 2 = a separate clause-major forward pass on x_in (fewer instructions in the
+ *              variable pass; faster for wide clauses and small candidate rows).
  * Results do not depend on the tuning beyond float32 summation order. Call gs_reserve again
  * after changing it if later calls are captured in a CUDA graph.
  */
@@ -176,6 +180,7 @@ typedef struct {
     int32_t var_lanes;
     int32_t fwd_lanes;
     int32_t var_gather;
+    int32_t loss_mode;
 } gs_tuning;
 
 /* gs_set_tuning / gs_get_tuning - set or read the caps above. Errors: GS_ERR_INVALID_ARG. */
@@ -185,7 +190,8 @@ gs_status gs_get_tuning(const gs_problem* prob, gs_tuning* tuning);
 /*
  * gs_autotune - pick the tuning for batches of B candidates stored as dtype by timing the fused
  * step (gs_step with grad = NULL and a loss) over the candidates-per-warp choices (lanes per
- * chunk) and both gather modes, and gs_forward over its lanes per chunk, on temporary buffers
+ * chunk) and both gather modes, gs_forward over its lanes per chunk, and the two loss modes of
+ * the fused step, on temporary buffers
  * it allocates and frees (n x B of each array). The fastest setting is applied to the problem
  * (gs_set_tuning), written to *out when out is not NULL, and the workspace is reserved for it.
  * Synchronous; not allowed during stream capture (GS_ERR_STATE). Errors: GS_ERR_INVALID_ARG,

@@ -55,7 +55,12 @@ class GsInfo(ctypes.Structure):
 
 
 class GsTuning(ctypes.Structure):
-    _fields_ = [("var_lanes", ctypes.c_int32), ("fwd_lanes", ctypes.c_int32), ("var_gather", ctypes.c_int32)]
+    _fields_ = [("var_lanes", ctypes.c_int32), ("fwd_lanes", ctypes.c_int32), ("var_gather", ctypes.c_int32),
+                ("loss_mode", ctypes.c_int32)]
+
+    def as_dict(self) -> dict:
+        return {"var_lanes": int(self.var_lanes), "fwd_lanes": int(self.fwd_lanes),
+                "var_gather": int(self.var_gather), "loss_mode": int(self.loss_mode)}
 
 
 class GsAdam(ctypes.Structure):
@@ -278,15 +283,16 @@ def gs_info_get(prob: Problem) -> dict:
     return prob.info()
 
 
-def gs_set_tuning(prob: Problem, var_lanes: int = 0, fwd_lanes: int = 0, var_gather: int = 0) -> None:
-    t = GsTuning(int(var_lanes), int(fwd_lanes), int(var_gather))
+def gs_set_tuning(prob: Problem, var_lanes: int = 0, fwd_lanes: int = 0, var_gather: int = 0,
+                  loss_mode: int = 0) -> None:
+    t = GsTuning(int(var_lanes), int(fwd_lanes), int(var_gather), int(loss_mode))
     _check(lib().gs_set_tuning(prob.handle, ctypes.byref(t)), "gs_set_tuning")
 
 
 def gs_get_tuning(prob: Problem) -> dict:
     t = GsTuning()
     _check(lib().gs_get_tuning(prob.handle, ctypes.byref(t)), "gs_get_tuning")
-    return {"var_lanes": int(t.var_lanes), "fwd_lanes": int(t.fwd_lanes), "var_gather": int(t.var_gather)}
+    return t.as_dict()
 
 
 def _dtype_arg(dtype) -> int:
@@ -301,7 +307,7 @@ def gs_autotune(prob: Problem, B: int, dtype, stream=None) -> dict:
     code = _dtype_arg(dtype)
     t = GsTuning()
     _check(lib().gs_autotune(prob.handle, int(B), code, _stream(stream), ctypes.byref(t)), "gs_autotune")
-    return {"var_lanes": int(t.var_lanes), "fwd_lanes": int(t.fwd_lanes), "var_gather": int(t.var_gather)}
+    return t.as_dict()
 
 
 def gs_reserve(prob: Problem, B: int, dtype) -> None:

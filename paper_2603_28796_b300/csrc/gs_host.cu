@@ -111,6 +111,7 @@ struct gs_problem {
     int var_lc_max = 32;
     int fwd_lc_max = 32;
     int var_gather = 0;
+    int loss_mode = 0;
 };
 
 namespace {
@@ -574,9 +575,11 @@ gs_status gs_set_tuning(gs_problem* p, const gs_tuning* t) {
     if (!ok(t->var_lanes) || !ok(t->fwd_lanes))
         return fail(GS_ERR_INVALID_ARG, "lanes per candidate chunk must be 0, 4, 8, 16 or 32");
     if (t->var_gather < 0 || t->var_gather > 2) return fail(GS_ERR_INVALID_ARG, "var_gather must be 0, 1 or 2");
+    if (t->loss_mode < 0 || t->loss_mode > 2) return fail(GS_ERR_INVALID_ARG, "loss_mode must be 0, 1 or 2");
     p->var_lc_max = t->var_lanes ? t->var_lanes : 32;
     p->fwd_lc_max = t->fwd_lanes ? t->fwd_lanes : 32;
     p->var_gather = t->var_gather;
+    p->loss_mode = t->loss_mode;
     return GS_OK;
 }
 
@@ -585,6 +588,7 @@ gs_status gs_get_tuning(const gs_problem* p, gs_tuning* t) {
     t->var_lanes = p->var_lc_max;
     t->fwd_lanes = p->fwd_lc_max;
     t->var_gather = p->var_gather;
+    t->loss_mode = p->loss_mode;
     return GS_OK;
 }
 
@@ -620,7 +624,7 @@ gs_status gs_autotune(gs_problem* p, int32_t B, gs_dtype dtype, gs_stream stream
         cleanup();
         return fail(GS_ERR_CUDA, "gs_autotune memset");
     }
-    const gs_tuning saved{p->var_lc_max, p->fwd_lc_max, p->var_gather};
+    const gs_tuning saved{p->var_lc_max, p->fwd_lc_max, p->var_gather, p->loss_mode};
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
@@ -676,6 +680,21 @@ gs_status gs_autotune(gs_problem* p, int32_t B, gs_dtype dtype, gs_stream stream
             best.fwd_lanes = lanes;
         }
     }
+    // loss inside the variable pass vs a separate forward pass, at the chosen widths
+    if (rs == GS_OK) {
+        p->var_lc_max = best.var_lanes;
+        p->var_gather = best.var_gather;
+        p->fwd_lc_max = best.fwd_lanes;
+        float mode_ms[3] = {-1.0f, -1.0f, -1.0f};
+        for (int mode = 1; mode <= 2 && rs == GS_OK; ++mode) {
+            p->loss_mode = mode;
+            if ((rs = ensure_ws(p, dtype, B, false, s)) != GS_OK) break;
+            mode_ms[mode] = timed([&] {
+                return gs_step(p, delta, m, v, nullptr, x0, x1, dtype, B, ldB, ++step, nullptr, loss, nullptr, stream);
+            });
+        }
+        best.loss_mode = (mode_ms[2] > 0.0f && mode_ms[1] > 0.0f && mode_ms[2] < mode_ms[1]) ? 2 : 1;
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     const cudaError_t se = cudaStreamSynchronize(s);
@@ -683,6 +702,7 @@ gs_status gs_autotune(gs_problem* p, int32_t B, gs_dtype dtype, gs_stream stream
     p->var_lc_max = saved.var_lanes;
     p->fwd_lc_max = saved.fwd_lanes;
     p->var_gather = saved.var_gather;
+    p->loss_mode = saved.loss_mode;
     if (rs != GS_OK) return rs;
     if (se != cudaSuccess) return cuda_fail(se, "gs_autotune");
     if ((st = gs_set_tuning(p, &best)) != GS_OK) return st;
@@ -819,6 +839,11 @@ gs_status gs_step(gs_problem* p, float* delta, float* m, float* v, const float* 
             GS_CUDA(launch_round(delta, reinterpret_cast<uint32_t*>(bits), p->h.n, B, ldB, nwords(B), s),
                     "round launch");
         return GS_OK;
+    }
+    if (loss && p->loss_mode == 2) {
+        // the loss at x_in from the clause-major forward pass, then the step without credits
+        if ((st = gs_forward(p, x_in, dtype, B, ldB, loss, stream)) != GS_OK) return st;
+        return var_pass(p, kModeAdam, x_in, dtype, B, ldB, nullptr, nullptr, delta, m, v, x_out, &k, nullptr, bits, s);
     }
     return var_pass(p, kModeAdam, x_in, dtype, B, ldB, nullptr, nullptr, delta, m, v, x_out, &k, loss, bits, s);
 }

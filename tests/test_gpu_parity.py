@@ -320,6 +320,7 @@ def test_autotune_picks_a_valid_tuning_and_keeps_results():
     B = 200
     t = _abi.gs_autotune(prob, B, "f32")
     assert t["var_lanes"] in (4, 8, 16, 32) and t["fwd_lanes"] in (4, 8, 16, 32) and t["var_gather"] in (1, 2)
+    assert t["loss_mode"] in (1, 2)
     assert _abi.gs_get_tuning(prob) == t
     x = H.device_cands(synth.uniform_values(cnf.n_vars, B, seed=9), B)
     loss = _abi.gs_forward(prob, x)
@@ -330,3 +331,31 @@ def test_autotune_picks_a_valid_tuning_and_keeps_results():
     H.assert_loss(loss.cpu().numpy()[0], lu)
     H.assert_grad(H.host64(grad), g_ref, scale)
     _abi.gs_set_tuning(prob)
+
+
+@pytest.mark.parametrize("name", ["mixed", "edge", "community"])
+@pytest.mark.parametrize("dtype", ["f32", "bf16"])
+def test_loss_modes_agree(name, dtype):
+    """The fused step's loss credited in the variable pass (loss_mode 1) or from a separate
+    forward pass (loss_mode 2): identical updates and rounded bits, both losses at the oracle's."""
+    cnf, prob = get(name)
+    n, B, t = cnf.n_vars, 100, 3
+    x0 = synth.uniform_values(n, B, seed=31)
+    d0 = synth.init_delta(n, B, seed=32)
+    outs = []
+    for mode in (1, 2):
+        _abi.gs_set_tuning(prob, loss_mode=mode)
+        xin = H.device_cands(x0, B, dtype)
+        delta, m, v = H.device_cands(d0, B), candidates(n, B), candidates(n, B)
+        xout = candidates(n, B, H.TORCH_DT[dtype])
+        bits = torch.zeros((n, 2), dtype=torch.int64, device="cuda")
+        loss = torch.zeros((1, B), dtype=torch.float64, device="cuda")
+        _abi.gs_step(prob, delta, m, v, t, x_in=xin, x_out=xout, loss=loss, bits=bits)
+        torch.cuda.synchronize()
+        outs.append((delta, m, v, xout, bits, loss))
+    _abi.gs_set_tuning(prob)
+    for a, b in zip(outs[0][:5], outs[1][:5]):
+        assert torch.equal(a, b)
+    lu, _ = oracle.forward(n, cnf.clause_ptr, cnf.lits, H.host64(H.device_cands(x0, B, dtype)))
+    for o in outs:
+        H.assert_loss(o[5].cpu().numpy()[0], lu)
