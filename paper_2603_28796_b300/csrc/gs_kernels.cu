@@ -184,6 +184,52 @@ __device__ __forceinline__ void st_vals(T* p, const float* x) {
     }
 }
 
+__device__ __forceinline__ float2 dup2(float a) { return make_float2(a, a); }
+
+// Literal factors f = a x + b of the VEC candidates in one 16-byte piece of a row, as pairs:
+// a = -1, b = 1 for a positive literal (1 - x), a = 1, b = 0 for a negated one (x). For 16-bit
+// values the product a x is formed by the mixed-precision FMA (16-bit a and x, float32 b and
+// result), which equals converting x to float32 first: a x is exact and the sum rounds once.
+template <typename T>
+__device__ __forceinline__ void factors(const uint4& r, float a, float b, float2 (&f)[Elem<T>::VEC / 2]);
+template <>
+__device__ __forceinline__ void factors<float>(const uint4& r, float a, float b, float2 (&f)[2]) {
+    f[0] = __ffma2_rn(dup2(a), make_float2(__uint_as_float(r.x), __uint_as_float(r.y)), dup2(b));
+    f[1] = __ffma2_rn(dup2(a), make_float2(__uint_as_float(r.z), __uint_as_float(r.w)), dup2(b));
+}
+__device__ __forceinline__ float2 fma_bf16_pair(uint32_t w, uint16_t a, float b) {
+    float lo, hi;
+    asm("{\n\t.reg .b16 l, h;\n\tmov.b32 {l, h}, %2;\n\t"
+        "fma.rn.f32.bf16 %0, %3, l, %4;\n\tfma.rn.f32.bf16 %1, %3, h, %4;\n\t}"
+        : "=f"(lo), "=f"(hi)
+        : "r"(w), "h"(a), "f"(b));
+    return make_float2(lo, hi);
+}
+__device__ __forceinline__ float2 fma_f16_pair(uint32_t w, uint16_t a, float b) {
+    float lo, hi;
+    asm("{\n\t.reg .b16 l, h;\n\tmov.b32 {l, h}, %2;\n\t"
+        "fma.rn.f32.f16 %0, %3, l, %4;\n\tfma.rn.f32.f16 %1, %3, h, %4;\n\t}"
+        : "=f"(lo), "=f"(hi)
+        : "r"(w), "h"(a), "f"(b));
+    return make_float2(lo, hi);
+}
+template <>
+__device__ __forceinline__ void factors<__nv_bfloat16>(const uint4& r, float a, float b, float2 (&f)[4]) {
+    const uint16_t ab = a < 0.0f ? 0xBF80u : 0x3F80u;   // -1 / +1 in bfloat16
+    f[0] = fma_bf16_pair(r.x, ab, b);
+    f[1] = fma_bf16_pair(r.y, ab, b);
+    f[2] = fma_bf16_pair(r.z, ab, b);
+    f[3] = fma_bf16_pair(r.w, ab, b);
+}
+template <>
+__device__ __forceinline__ void factors<__half>(const uint4& r, float a, float b, float2 (&f)[4]) {
+    const uint16_t ab = a < 0.0f ? 0xBC00u : 0x3C00u;   // -1 / +1 in float16
+    f[0] = fma_f16_pair(r.x, ab, b);
+    f[1] = fma_f16_pair(r.y, ab, b);
+    f[2] = fma_f16_pair(r.z, ab, b);
+    f[3] = fma_f16_pair(r.w, ab, b);
+}
+
 __device__ __forceinline__ void kahan_add(float& s, float& c, float x) {
     const float y = x - c;
     const float t = s + y;
@@ -230,7 +276,6 @@ __device__ __forceinline__ void group_sum(float (&a)[N]) {
 // Literal factor f = a * x + b on two candidates at once (packed f32x2 arithmetic):
 // (a, b) = (-1, 1) for a positive literal (f = 1 - x), (1, 0) for a negated one (f = x),
 // (0, 1) for the unit-clause sentinel (f = 1, nothing loaded).
-__device__ __forceinline__ float2 dup2(float a) { return make_float2(a, a); }
 
 __device__ __forceinline__ void code_ab(uint32_t c, float& a, float& b) {
     const bool sent = (c >> kVShift) == kVSentinel;
@@ -284,19 +329,21 @@ __device__ __forceinline__ void var_slots(const uint32_t* cd, int cs, int ce, co
         }
 #pragma unroll
         for (int j = 0; j < NB; ++j) {
-            float xv[VEC];
-            unpack<T>(raw[j], xv);
             const uint32_t c = cw[j];
             float a, b;
             code_ab(c, a, b);
+            float2 f[H];
+            factors<T>(raw[j], a, b, f);
             const bool end = (c & kVEnd) != 0u;
             const float sg = end ? occ_sign(c) : 0.0f;
+            const float e1 = end ? 1.0f : 0.0f;   // restart the running product after an end:
+            const float keep = 1.0f - e1;         // R = rn * keep + e1 (rn is finite)
             float2 rn[H];
 #pragma unroll
             for (int h = 0; h < H; ++h) {
-                rn[h] = __fmul2_rn(R[h], __ffma2_rn(dup2(a), make_float2(xv[2 * h], xv[2 * h + 1]), dup2(b)));
+                rn[h] = __fmul2_rn(R[h], f[h]);
                 G2[h] = __ffma2_rn(dup2(sg), rn[h], G2[h]);
-                R[h] = end ? dup2(1.0f) : rn[h];
+                R[h] = __ffma2_rn(rn[h], dup2(keep), dup2(e1));
             }
             if (LOSS) {
                 const uint32_t f = c & (kVEnd | kVCredit | kVSelfNeg);
@@ -347,15 +394,12 @@ __device__ __forceinline__ void occ_batch(const uint32_t* cd, int s, int ce, con
         float2 prod[H];
 #pragma unroll
         for (int j = 0; j < K; ++j) {
-            float xv[VEC];
-            unpack<T>(raw[o * K + j], xv);
             float a, b;
             fixed_ab<(TAIL ? 1 : K)>(cw[o * K + j], a, b);
+            float2 f[H];
+            factors<T>(raw[o * K + j], a, b, f);
 #pragma unroll
-            for (int h = 0; h < H; ++h) {
-                const float2 f = __ffma2_rn(dup2(a), make_float2(xv[2 * h], xv[2 * h + 1]), dup2(b));
-                prod[h] = (j == 0) ? f : __fmul2_rn(prod[h], f);
-            }
+            for (int h = 0; h < H; ++h) prod[h] = (j == 0) ? f[h] : __fmul2_rn(prod[h], f[h]);
         }
         const uint32_t last = cw[o * K + K - 1];
         const bool valid = !TAIL || (s + o * K) < ce;
@@ -983,15 +1027,18 @@ __device__ __forceinline__ void fwd_slots(const uint32_t* cd, int cs, int ce, co
         }
 #pragma unroll
         for (int j = 0; j < NB; ++j) {
-            float xv[VEC];
-            unpack<T>(raw[j], xv);
             const uint32_t c = cw[j];
-            const bool pad = (c == kPad);
+            const bool pad = (c == kPad);   // raw is zero: factor b = 1
             const float a = pad ? 0.0f : ((c & kFNeg) ? 1.0f : -1.0f);
             const float b = pad ? 1.0f : ((c & kFNeg) ? 0.0f : 1.0f);
             const bool end = !pad && (c & kFEnd);
+            float2 f[VEC / 2];
+            factors<T>(raw[j], a, b, f);
 #pragma unroll
-            for (int e = 0; e < VEC; ++e) R[e] *= fmaf(a, xv[e], b);
+            for (int e = 0; e < VEC; e += 2) {
+                R[e] *= f[e / 2].x;
+                R[e + 1] *= f[e / 2].y;
+            }
             if (end) {
 #pragma unroll
                 for (int e = 0; e < VEC; ++e) {
