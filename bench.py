@@ -489,7 +489,7 @@ def run_native(args):
     import torch.distributed as dist
 
     from paper_2603_28796_b300 import _abi, synth
-    from paper_2603_28796_b300.engine import Engine
+    from paper_2603_28796_b300.engine import Engine, candidates
 
     from paper_2603_28796_b300 import shard
 
@@ -590,26 +590,49 @@ def run_native(args):
     if not args.no_e2e:
         # End to end through the public API with host buffers: every step copies that step's
         # candidate logits from pinned host memory to the device, runs the step and the check,
-        # and reads back the per-candidate loss and unsat counts into pinned host memory.
+        # and reads back the per-candidate loss and unsat counts into pinned host memory. The
+        # copy of step k + 1's logits runs on a second stream into a second buffer while step k
+        # computes (the copy waits only for the step that last used that buffer).
         Ke = max(3, min(K, 20))
         host_delta = torch.from_numpy(synth.init_delta(n, B, seed=77 + rank)).pin_memory()
         host_loss = torch.empty((1, B), dtype=torch.float64).pin_memory()
         host_unsat = torch.empty((1, B), dtype=torch.int32).pin_memory()
+        dbuf = [eng.delta, candidates(n, B)]
+        copy_stream = torch.cuda.Stream()
+        main = torch.cuda.current_stream()
+        copied = [torch.cuda.Event() for _ in range(2)]
+        used = [torch.cuda.Event() for _ in range(2)]
         torch.cuda.synchronize()
         a0 = torch.cuda.Event(enable_timing=True)
         a1 = torch.cuda.Event(enable_timing=True)
         a0.record()
-        for _ in range(Ke):
-            eng.delta.copy_(host_delta[:, :B], non_blocking=True)
+        copy_stream.wait_stream(main)
+        with torch.cuda.stream(copy_stream):
+            dbuf[0].copy_(host_delta[:, :B], non_blocking=True)
+            copied[0].record(copy_stream)
+        for k in range(Ke):
+            cur = k % 2
+            if k + 1 < Ke:
+                with torch.cuda.stream(copy_stream):
+                    if k >= 1:
+                        copy_stream.wait_event(used[cur ^ 1])
+                    dbuf[cur ^ 1].copy_(host_delta[:, :B], non_blocking=True)
+                    copied[cur ^ 1].record(copy_stream)
+            main.wait_event(copied[cur])
+            eng.delta = dbuf[cur]
             eng.step()
+            used[cur].record(main)
             host_loss.copy_(eng.loss, non_blocking=True)
             host_unsat.copy_(eng.unsat, non_blocking=True)
         a1.record()
         torch.cuda.synchronize()
+        eng.delta = dbuf[0]
         e_ms = a0.elapsed_time(a1)
         e_ms = shard.max_over_ranks(e_ms, device=dev)
         e2e = {"value": evals_per_step * Ke * world / (e_ms / 1000.0), "unit": "evals/s",
-               "h2d_bytes_per_step": n * B * 4, "d2h_bytes_per_step": B * 8 + B * 4, "steps": Ke}
+               "h2d_bytes_per_step": n * B * 4, "d2h_bytes_per_step": B * 8 + B * 4, "steps": Ke,
+               "h2d_GBps": n * B * 4 * Ke / (e_ms / 1000.0) / 1e9,
+               "overlap": "copy of step k+1's inputs on a second stream during step k"}
 
     legs = None
     if rank == 0 and world == 1 and args.legs not in ("", "none"):
