@@ -13,7 +13,7 @@ constexpr uint32_t kPhW0 = 0x9E3779B9u;   // Weyl increments of the key
 constexpr uint32_t kPhW1 = 0xBB67AE85u;
 
 __device__ __forceinline__ void philox4x32_10(uint32_t (&x)[4], uint32_t k0, uint32_t k1) {
-#pragma unroll
+#pragma unroll 2   // smaller code: the straight-through kernel is otherwise instruction-fetch bound
     for (int r = 0; r < 10; ++r) {
         const uint64_t p0 = static_cast<uint64_t>(kPhM0) * x[0];
         const uint64_t p1 = static_cast<uint64_t>(kPhM1) * x[2];
