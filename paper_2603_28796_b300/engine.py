@@ -140,6 +140,24 @@ class Engine:
             for _ in range(steps):
                 self.step(loss, check)
 
+    def state_dict(self) -> dict:
+        """Everything the next step reads: logits, Adam moments, the current relaxed values, the
+        step counter and the ping-pong index (host copies; torch.save-able)."""
+        return {"kind": "relaxed", "n": self.n, "B": self.B, "dtype": str(self.dtype), "t": self.t,
+                "delta": self.delta.detach().cpu().clone(), "m": self.m.detach().cpu().clone(),
+                "v": self.v.detach().cpu().clone(), "x": self.x[self.cur].detach().cpu().clone()}
+
+    def load_state_dict(self, st: dict) -> None:
+        """Resume from state_dict(): the following steps are bitwise those of the saved run."""
+        if st.get("kind") != "relaxed" or st["n"] != self.n or st["B"] != self.B or st["dtype"] != str(self.dtype):
+            raise ValueError("state does not match this engine (kind, n, B, dtype)")
+        self.delta.copy_(st["delta"].to(self.device))
+        self.m.copy_(st["m"].to(self.device))
+        self.v.copy_(st["v"].to(self.device))
+        self.cur = 0
+        self.x[0].copy_(st["x"].to(self.device))
+        self.t = int(st["t"])
+
     def round_check(self):
         """Fresh rounding + check of the current delta: (unsat [n_inst, B], best [n_inst])."""
         return _abi.gs_round_check(self.prob, self.delta, bits=self.bits, unsat=self.unsat, best=self.best)
@@ -210,6 +228,32 @@ class STEngine:
                         noise=ring[self.cur] if ring is not None else None,
                         noise_next_out=ring[self.cur ^ 1] if ring is not None else None)
         self.cur ^= 1
+
+    def state_dict(self) -> dict:
+        """Logits, Adam moments, the hard assignment of the next step, its noise (ring), the step
+        counter and the noise seed (host copies; the noise stream itself is a pure function of
+        (seed, step), so nothing else is needed to continue bitwise)."""
+        st = {"kind": "straight-through", "n": self.n, "B": self.B, "t": self.t, "noise_seed": self.noise_seed,
+              "delta": self.delta.detach().cpu().clone(), "m": self.m.detach().cpu().clone(),
+              "v": self.v.detach().cpu().clone(), "bits": self.bits[self.cur].detach().cpu().clone()}
+        if self.noise is not None:
+            st["noise"] = self.noise[self.cur].detach().cpu().clone()
+        return st
+
+    def load_state_dict(self, st: dict) -> None:
+        if st.get("kind") != "straight-through" or st["n"] != self.n or st["B"] != self.B:
+            raise ValueError("state does not match this engine (kind, n, B)")
+        if (self.noise is not None) != ("noise" in st):
+            raise ValueError("noise ring setting differs from the saved run")
+        self.delta.copy_(st["delta"].to(self.device))
+        self.m.copy_(st["m"].to(self.device))
+        self.v.copy_(st["v"].to(self.device))
+        self.cur = 0
+        self.bits[0].copy_(st["bits"].to(self.device))
+        if self.noise is not None:
+            self.noise[0].copy_(st["noise"].to(self.device))
+        self.t = int(st["t"])
+        self.noise_seed = int(st["noise_seed"])
 
     def capture(self, steps: int, check: bool = True) -> torch.cuda.CUDAGraph:
         if steps % 2:

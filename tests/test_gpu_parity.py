@@ -359,3 +359,69 @@ def test_loss_modes_agree(name, dtype):
     lu, _ = oracle.forward(n, cnf.clause_ptr, cnf.lits, H.host64(H.device_cands(x0, B, dtype)))
     for o in outs:
         H.assert_loss(o[5].cpu().numpy()[0], lu)
+
+
+def test_checkpoint_resume_is_bitwise():
+    """N steps == k steps, state_dict() through torch.save / torch.load, a fresh engine, N - k steps."""
+    import io
+    cnf, prob = get("mixed")
+    B = 96
+    ref = Engine(prob, B, "bf16", seed=4)
+    for _ in range(7):
+        ref.step()
+    a = Engine(prob, B, "bf16", seed=4)
+    for _ in range(3):
+        a.step()
+    buf = io.BytesIO()
+    torch.save(a.state_dict(), buf)
+    buf.seek(0)
+    b = Engine(prob, B, "bf16", seed=99)
+    b.load_state_dict(torch.load(buf))
+    for _ in range(4):
+        b.step()
+    torch.cuda.synchronize()
+    for x, y in ((ref.delta, b.delta), (ref.m, b.m), (ref.v, b.v), (ref.x_cur, b.x_cur), (ref.bits, b.bits),
+                 (ref.loss, b.loss), (ref.unsat, b.unsat)):
+        assert torch.equal(x, y)
+
+
+def test_hub_variable_with_100k_occurrences():
+    """One variable in every one of 100,000 clauses: its occurrence list is split into hundreds
+    of tile parts combined by the last part to finish."""
+    rng = np.random.default_rng(12)
+    n, m = 5000, 100_000
+    others = rng.integers(2, n + 1, size=(m, 2))
+    others[:, 1] = np.where(others[:, 1] == others[:, 0], (others[:, 0] % (n - 1)) + 2, others[:, 1])
+    signs = np.where(rng.random((m, 3)) < 0.5, 1, -1)
+    lits = (np.concatenate([np.ones((m, 1), dtype=np.int64), others], axis=1) * signs).astype(np.int32).ravel()
+    cp = np.arange(0, 3 * m + 1, 3, dtype=np.int64)
+    cnf = synth.CNF(n, cp, lits)
+    prob = H.load(cnf)
+    assert prob.info()["n_split"] >= 1
+    B = 64
+    x = synth.uniform_values(n, B, seed=13)
+    g = _abi.gs_backward(prob, H.device_cands(x, B))
+    torch.cuda.synchronize()
+    g_ref, scale = oracle.backward(n, cp, lits, x.astype(np.float64))
+    H.assert_grad(H.host64(g), g_ref, scale)
+
+
+def test_allocation_failure_is_reported():
+    """A workspace request far beyond the device's memory (thousands of tiles x 2^27 candidates,
+    terabytes of loss partials) fails cleanly with GS_ERR_OOM at its first allocation, and the
+    problem stays usable."""
+    cnf = synth.planted_ksat(5000, 40000, 8, seed=3)
+    prob = H.load(cnf)
+    assert prob.info()["n_var_tiles"] * (1 << 27) * 4 > 2 * 10 ** 12
+    try:
+        with pytest.raises(_abi.GSError) as ei:
+            _abi.gs_reserve(prob, 1 << 27, "f32")
+        assert ei.value.status == 3          # GS_ERR_OOM
+        B = 64
+        x = H.device_cands(synth.uniform_values(cnf.n_vars, B, seed=1), B)
+        loss = _abi.gs_forward(prob, x)
+        torch.cuda.synchronize()
+        lu, _ = oracle.forward(cnf.n_vars, cnf.clause_ptr, cnf.lits, H.host64(x))
+        H.assert_loss(loss.cpu().numpy()[0], lu)
+    finally:
+        prob.close()

@@ -218,3 +218,26 @@ def test_noise_ring_equals_generated_noise():
     a, b = engines
     for x, y in ((a.delta, b.delta), (a.m, b.m), (a.v, b.v), (a.bits_cur, b.bits_cur), (a.unsat, b.unsat)):
         assert torch.equal(x, y)
+
+
+def test_st_checkpoint_resume_is_bitwise():
+    import io
+    n, cp, lits, prob = problem("mixed")
+    B = 70
+    ref = STEngine(prob, B, seed=1, noise_seed=5)
+    for _ in range(6):
+        ref.step()
+    a = STEngine(prob, B, seed=1, noise_seed=5)
+    for _ in range(2):
+        a.step()
+    buf = io.BytesIO()
+    torch.save(a.state_dict(), buf)
+    buf.seek(0)
+    b = STEngine(prob, B, seed=8, noise_seed=77)
+    b.load_state_dict(torch.load(buf))
+    for _ in range(4):
+        b.step()
+    torch.cuda.synchronize()
+    for x, y in ((ref.delta, b.delta), (ref.m, b.m), (ref.v, b.v), (ref.bits_cur, b.bits_cur),
+                 (ref.unsat, b.unsat)):
+        assert torch.equal(x, y)
