@@ -241,3 +241,42 @@ def test_st_checkpoint_resume_is_bitwise():
     for x, y in ((ref.delta, b.delta), (ref.m, b.m), (ref.v, b.v), (ref.bits_cur, b.bits_cur),
                  (ref.unsat, b.unsat)):
         assert torch.equal(x, y)
+
+
+def test_st_step_on_a_batch_of_instances():
+    """A batch of uneven instances loaded as one problem: rows are instance-concatenated, each
+    instance's literals local to it; the step equals the oracle run on each instance alone."""
+    batch = synth.uneven_batch(5, n_min=60, n_max=400, seed=3)
+    prob = _abi.gs_load_batch(batch.n_vars, batch.n_clauses, batch.clause_ptr, batch.lits)
+    n = int(sum(batch.n_vars))
+    B, t = 70, 2
+    d0 = synth.init_delta(n, B, seed=4)
+    l0 = oracle.logistic_noise(n, B, 8, t)[0].astype(np.float32)
+    l1 = oracle.logistic_noise(n, B, 8, t + 1)[0].astype(np.float32)
+    delta, m, v = H.device_cands(d0, B), candidates(n, B), candidates(n, B)
+    bits_in = torch.zeros((n, 2), dtype=torch.int64, device="cuda")
+    bits_out = torch.zeros((n, 2), dtype=torch.int64, device="cuda")
+    _abi.gs_st_sample(prob, delta, bits_in, noise=H.device_cands(l0, B))
+    unsat = torch.zeros((5, B), dtype=torch.int32, device="cuda")
+    _abi.gs_check_bits(prob, bits_in, B, unsat)
+    _abi.gs_st_step(prob, delta, m, v, bits_in, bits_out, t, noise=H.device_cands(l0, B),
+                    noise_next=H.device_cands(l1, B))
+    torch.cuda.synchronize()
+    got_d = H.host64(delta)
+    got_bits = H.unpack_bits(bits_out, n, B)
+    u = unsat.cpu().numpy()
+    r0 = 0
+    z = np.zeros((n, B))
+    for i in range(5):
+        inst = batch.instance(i)
+        ni = inst.n_vars
+        rows = slice(r0, r0 + ni)
+        ref = oracle.st_step(ni, inst.clause_ptr, inst.lits, d0[rows], z[rows], z[rows], l0[rows], l1[rows], t)
+        assert np.array_equal(u[i], ref["unsat"])
+        zi = d0[rows].astype(np.float64) + l0[rows].astype(np.float64)
+        zerr = 2 * U * (np.abs(d0[rows]) + np.abs(l0[rows]))
+        tol = H.adam_tolerances(d0[rows], z[rows], z[rows], ref["grad"], 0.0, t, g_rel=0.0, z=zi, z_err=zerr)
+        assert np.all(np.abs(got_d[rows] - ref["delta"]) <= tol["delta"] + 1e-38)
+        tie = np.abs(ref["delta"] + l1[rows].astype(np.float64)) <= tol["delta"] + 1e-30
+        assert np.array_equal(got_bits[rows][~tie], ref["x_hat_next"][~tie])
+        r0 += ni
