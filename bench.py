@@ -45,9 +45,9 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle sample")
     ap.add_argument("--no-autotune", action="store_true", help="skip gs_autotune (use defaults / --var-* flags)")
-    ap.add_argument("--legs", default="st,precision,tseitin,plain,structured",
-                    help="extra single-GPU measurements added to the line under 'legs' (comma list of st, precision, "
-                         "tseitin, plain, structured, batching; 'none' for none)")
+    ap.add_argument("--legs", default="st,pool,precision,tseitin,plain,structured",
+                    help="extra single-GPU measurements added to the line under 'legs' (comma list of st, pool, "
+                         "precision, tseitin, plain, structured, batching; 'none' for none)")
     ap.add_argument("--leg-steps", type=int, default=50, help="timed steps of each extra leg")
     ap.add_argument("--var-lanes", type=int, default=0, help="cap on lanes per candidate chunk (gs_set_tuning)")
     ap.add_argument("--var-gather", type=int, default=0, help="0: automatic, 1: register loads, 2: TMA gather4 ring (gs_set_tuning)")
@@ -384,6 +384,46 @@ def leg_tseitin(torch, args, peak):
     return out
 
 
+def leg_pool(torch, args, peak):
+    """Candidate pool and branching variables (Eq. 9, Lemma 1) on the differentiation workload after
+    a few straight-through steps: N = 100 noisy samples of the highest-loss candidate with the top
+    0.05 % most confident variables of each, and the d = 7 least confident variables."""
+    from paper_2603_28796_b300 import _abi, pool
+    from paper_2603_28796_b300.engine import STEngine
+
+    cnf, B, _, desc = workload_setup("differentiation")
+    prob = _abi.gs_load_cnf(cnf.n_vars, cnf.clause_ptr, cnf.lits)
+    eng = STEngine(prob, B, seed=51, noise_seed=53)
+    eng.run(20, graph=False)
+    torch.cuda.synchronize()
+    b_sel = pool.select_candidate(eng.unsat.cpu().numpy()[0], "max")
+    N, S, d = pool.DEFAULT_N, pool.selection_size(cnf.n_vars), pool.DEFAULT_D
+
+    def timed(fn, k=10):
+        for _ in range(2):
+            fn()
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(k):
+            fn()
+        b.record()
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / k
+
+    ms_pool = timed(lambda: _abi.gs_pool_sample(prob, eng.delta, b_sel, N, S, seed=7))
+    ms_branch = timed(lambda: _abi.gs_branch_vars(prob, eng.delta, b_sel, d))
+    out = {"workload": desc + ", straight-through state after 20 steps", "N": N, "S": S, "d": d,
+           "pool_ms": ms_pool, "pool_keys_per_s": cnf.n_vars * N / (ms_pool / 1000.0),
+           "branch_ms": ms_branch, "b_sel": b_sel,
+           "method": "4-pass radix select of unique 64-bit keys, in-kernel Philox noise"}
+    del eng
+    prob.close()
+    torch.cuda.empty_cache()
+    return out
+
+
 def leg_st(torch, args, peak):
     """The paper's own training forward on the differentiation workload: straight-through Gumbel
     (hard assignment in the forward pass, soft chain in the backward pass, noise drawn in the
@@ -443,6 +483,8 @@ def run_legs(torch, args, peak):
                 legs[name] = leg_st(torch, args, peak)
             elif name == "tseitin":
                 legs[name] = leg_tseitin(torch, args, peak)
+            elif name == "pool":
+                legs[name] = leg_pool(torch, args, peak)
             elif name == "batching":
                 legs[name] = leg_batching(torch, args, peak)
             else:
