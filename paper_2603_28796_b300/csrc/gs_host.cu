@@ -44,7 +44,10 @@ gs_status upload(const std::vector<T>& h, T** d, int64_t* bytes, cudaStream_t s)
     // +64 B of zero padding: 16-byte bulk copies may round a tile's range up past the end.
     const size_t nb = h.size() * sizeof(T) + 64;
     void* p = nullptr;
-    if (cudaMalloc(&p, nb) != cudaSuccess) return fail(GS_ERR_OOM, "cudaMalloc of index structures failed");
+    if (cudaMalloc(&p, nb) != cudaSuccess) {
+        cudaGetLastError();   // an allocation failure is reported here, not by a later launch check
+        return fail(GS_ERR_OOM, "cudaMalloc of index structures failed");
+    }
     *d = static_cast<T*>(p);
     *bytes += static_cast<int64_t>(nb);
     GS_CUDA(cudaMemsetAsync(p, 0, nb, s), "cudaMemsetAsync");
@@ -149,7 +152,10 @@ gs_status grow(T** ptr, size_t* cap, size_t need, cudaStream_t s, bool in_captur
         *cap = 0;
     }
     void* p = nullptr;
-    if (cudaMalloc(&p, need * sizeof(T)) != cudaSuccess) return fail(GS_ERR_OOM, std::string("workspace ") + what);
+    if (cudaMalloc(&p, need * sizeof(T)) != cudaSuccess) {
+        cudaGetLastError();   // an allocation failure is reported here, not by a later launch check
+        return fail(GS_ERR_OOM, std::string("workspace ") + what);
+    }
     *ptr = static_cast<T*>(p);
     *cap = need;
     return GS_OK;
@@ -609,8 +615,10 @@ gs_status gs_autotune(gs_problem* p, int32_t B, gs_dtype dtype, gs_stream stream
     const size_t es = (static_cast<int>(dtype) == kF32) ? 4 : 2;
     const size_t fbytes = static_cast<size_t>(n) * ldB * 4, xbytes = static_cast<size_t>(n) * ldB * es;
     void* mem = nullptr;
-    if (cudaMalloc(&mem, 3 * fbytes + 2 * xbytes + static_cast<size_t>(B) * 8 + 256) != cudaSuccess)
+    if (cudaMalloc(&mem, 3 * fbytes + 2 * xbytes + static_cast<size_t>(B) * 8 + 256) != cudaSuccess) {
+        cudaGetLastError();
         return fail(GS_ERR_OOM, "gs_autotune temporaries");
+    }
     char* base = static_cast<char*>(mem);
     float* delta = reinterpret_cast<float*>(base);
     float* m = reinterpret_cast<float*>(base + fbytes);

@@ -180,9 +180,19 @@ gs_status validate(int32_t n_inst, const int64_t* n_vars, const int64_t* n_claus
     return GS_OK;
 }
 
+// Small formulas get smaller tiles so that enough warps have work: a formula of m clauses (n
+// variables) is cut into at least about kMinTiles clause (occurrence) tiles when it is small
+// enough, by capping the clauses (variables) per tile; large formulas hit the code limits first.
+constexpr int64_t kMinTiles = 2048;
+int tile_cap(int64_t count, int cap) {
+    const int64_t want = (count + kMinTiles - 1) / kMinTiles;
+    return static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(cap, want)));
+}
+
 // Clause tiles: consecutive whole clauses of one instance, <= kFwdCodes codes, <= kFwdClauses.
 // One code per literal in literal order, so a tile's codes start at its first clause's offset.
 void build_fwd(const int64_t* clause_ptr, const int32_t* lits, HostPlan& P) {
+    const int clause_cap = tile_cap(P.m, kFwdClauses);
     std::vector<int64_t> first;   // first clause of each tile
     P.f_iptr.assign(P.n_inst + 1, 0);
     int64_t ctab = 0;
@@ -196,7 +206,7 @@ void build_fwd(const int64_t* clause_ptr, const int32_t* lits, HostPlan& P) {
             it.inst = inst;
             first.push_back(t);
             int nc = 0, ncodes = 0;
-            while (t < te && nc < kFwdClauses) {
+            while (t < te && nc < clause_cap) {
                 const int k = static_cast<int>(clause_ptr[t + 1] - clause_ptr[t]);
                 if (ncodes + k > kFwdCodes) break;
                 ncodes += k;
@@ -320,6 +330,7 @@ gs_status build_var(const int64_t* clause_ptr, const int32_t* lits, HostPlan& P)
     const uint32_t* codes = P.vcodes.data();
 
     // Sequential partition into tiles (creation order = storage order of recs and vtab).
+    const int var_cap = tile_cap(n, kVarVars);
     struct Pending {
         size_t made;
         int64_t cost;     // codes of the whole split variable (ordering key)
@@ -382,7 +393,7 @@ gs_status build_var(const int64_t* clause_ptr, const int32_t* lits, HostPlan& P)
                 P.n_split_rows += pi;
                 continue;
             }
-            if (open && (cur.nv == kVarVars || cur.n_codes + cost(v) > kVarCodes)) close_item();
+            if (open && (cur.nv == var_cap || cur.n_codes + cost(v) > kVarCodes)) close_item();
             if (!open) {
                 cur = VarItem{};
                 cur.code_base = code_start[v];
