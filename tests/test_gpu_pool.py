@@ -96,3 +96,27 @@ def test_pool_rejects_bad_sizes():
         _abi.gs_pool_sample(prob, delta, 0, 0, 1)              # N < 1
     with pytest.raises(_abi.GSError):
         _abi.gs_branch_vars(prob, delta, 0, 0)
+
+
+def test_dimacs_writer_round_trip(tmp_path):
+    """An augmented formula written by pool.dimacs loads back through gs_load_dimacs with the
+    formula's clauses plus one unit clause per selected variable."""
+    cnf, prob = problem(300)
+    units = [5, -17, 300]
+    path = tmp_path / "aug.cnf"
+    path.write_text(pool.dimacs(cnf.n_vars, cnf.clause_ptr, cnf.lits, units, comment="round trip"))
+    p2 = _abi.gs_load_dimacs(str(path))
+    info = p2.info()
+    assert info["n_vars"] == cnf.n_vars and info["n_clauses"] == cnf.n_clauses + 3
+    assert info["nnz"] == cnf.nnz + 3 and info["n_unit"] == 3
+    # the planted assignment with the units' values forced: unsat counts agree with a host count
+    x = cnf.xstar.copy()
+    x[4], x[16], x[299] = 1, 0, 1
+    B = 1
+    d = np.where(x[:, None] == 1, 1.0, -1.0).astype(np.float32)
+    unsat, _ = _abi.gs_round_check(p2, H.device_cands(d, B))
+    torch.cuda.synchronize()
+    lits = cnf.lits.astype(np.int64)
+    true = np.where(lits > 0, x[np.abs(lits) - 1] == 1, x[np.abs(lits) - 1] == 0)
+    want = int((~np.logical_or.reduceat(true, cnf.clause_ptr[:-1])).sum())
+    assert int(unsat.cpu().numpy()[0, 0]) == want
