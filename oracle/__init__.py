@@ -9,7 +9,8 @@ calls the plain C implementation in ``oracle.c``; see that file for the equation
 follows (Eq. 1-5 and the experiment-setup hyper-parameters of the paper).
 
 Arrays of candidate values are var-major, shape ``[n, B]``: row v holds variable v of every
-candidate. Parity status: all functions pinned (see ``tests/test_oracle_pins.py``).
+candidate. Parity status: all functions pinned (``tests/test_oracle_pins.py``,
+``tests/test_oracle_st_pins.py``, ``tests/test_oracle_pool_pins.py``).
 """
 from __future__ import annotations
 

@@ -22,7 +22,8 @@
  * of every sum inside one candidate is the plain order written here.
  *
  * Parity status: every function below is pinned by the tests (brute-force enumeration, the
- * paper's worked examples, finite differences, closed forms, torch autograd + torch.optim.Adam).
+ * paper's worked examples, finite differences, closed forms, torch autograd + torch.optim.Adam,
+ * the noise generator's published known-answer vectors and the logistic law).
  */
 #include <math.h>
 #include <stdint.h>
