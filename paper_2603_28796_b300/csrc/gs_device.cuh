@@ -87,6 +87,19 @@ __device__ __forceinline__ Span span16(const void* p, uint32_t bytes) {
     return s;
 }
 
+// Called once by every thread of every CTA of a work-queue kernel, after its loop: the last CTA
+// to leave rewinds the queue (head and exit count back to 0), so the next launch needs no reset.
+__device__ __forceinline__ void queue_exit(int32_t* head, int32_t* exit_cnt) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        if (atomicAdd(exit_cnt, 1) == static_cast<int>(gridDim.x) - 1) {
+            atomicExch(head, 0);
+            atomicExch(exit_cnt, 0);
+        }
+    }
+}
+
 __device__ __forceinline__ int fetch_work(int32_t* head, int lane) {
     int w = 0;
     if (lane == 0) w = atomicAdd(head, 1);

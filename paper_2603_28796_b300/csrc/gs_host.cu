@@ -161,6 +161,16 @@ gs_status grow(T** ptr, size_t* cap, size_t need, cudaStream_t s, bool in_captur
     return GS_OK;
 }
 
+// The work-queue control words must be zero between launches (the kernels keep them so); a
+// fresh allocation is cleared once.
+gs_status grow_ctl(gs_problem* p, size_t need, cudaStream_t s, bool in_capture) {
+    const int32_t* before = p->ctl;
+    gs_status st = grow(&p->ctl, &p->ctl_cap, need, s, in_capture, "counters");
+    if (st != GS_OK) return st;
+    if (p->ctl != before) GS_CUDA(cudaMemsetAsync(p->ctl, 0, sizeof(int32_t) * p->ctl_cap, s), "clear counters");
+    return GS_OK;
+}
+
 gs_status ensure_ws(gs_problem* p, int dtype, int32_t B, bool need_bits, cudaStream_t s) {
     const bool cap = capturing(s);
     const Chunking cv = chunking_for(dtype, B, p->var_lc_max);
@@ -173,9 +183,7 @@ gs_status ensure_ws(gs_problem* p, int dtype, int32_t B, bool need_bits, cudaStr
     if ((st = grow(&p->split, &p->split_cap, std::max<size_t>(1, static_cast<size_t>(p->h.n_split_rows) * cv.bpad), s,
                    cap, "split partials")) != GS_OK)
         return st;
-    if ((st = grow(&p->ctl, &p->ctl_cap, 4 + static_cast<size_t>(p->h.n_split) * cv.n_chunks, s, cap, "counters")) !=
-        GS_OK)
-        return st;
+    if ((st = grow_ctl(p, kCtlSplit + static_cast<size_t>(p->h.n_split) * cv.n_chunks, s, cap)) != GS_OK) return st;
     if (need_bits) {
         if ((st = grow(&p->bits, &p->bits_cap, std::max<size_t>(1, static_cast<size_t>(p->h.n) * nwords(B)), s, cap,
                        "bits")) != GS_OK)
@@ -329,9 +337,9 @@ gs_status launch_check_all(gs_problem* p, const uint64_t* bits, int32_t B, int32
     cp.bits = bits;
     cp.part16 = p->part16;
     cp.bpad16 = nwd * 64;
-    cp.head = p->ctl + 2;
+    cp.head = p->ctl + kCtlCheckHead;
+    cp.exit_cnt = p->ctl + kCtlCheckExit;
     cp.status = p->status;
-    GS_CUDA(cudaMemsetAsync(p->ctl + 2, 0, sizeof(int32_t), s), "memset head");
     const int64_t total = static_cast<int64_t>(cp.n_items) * cp.n_wchunks;
     if (total > 0 && B > 0) {
         const int grid = static_cast<int>(std::min<int64_t>(grid_check(lw), total));
@@ -397,7 +405,7 @@ gs_status ensure_st_ws(gs_problem* p, int32_t B, cudaStream_t s) {
     if ((st = grow(&p->split, &p->split_cap, std::max<size_t>(1, static_cast<size_t>(p->h.n_split_rows) * c.bpad), s,
                    cap, "split partials")) != GS_OK)
         return st;
-    return grow(&p->ctl, &p->ctl_cap, 4 + static_cast<size_t>(p->h.n_split) * c.n_chunks, s, cap, "counters");
+    return grow_ctl(p, kCtlSplit + static_cast<size_t>(p->h.n_split) * c.n_chunks, s, cap);
 }
 
 gs_status var_pass(gs_problem* p, int mode, const void* x_in, int dtype, int32_t B, int64_t ldB, const double* dloss,
@@ -428,11 +436,10 @@ gs_status var_pass(gs_problem* p, int mode, const void* x_in, int dtype, int32_t
     if (k) vp.adam = *k;
     vp.loss_part = loss ? p->part : nullptr;
     vp.split_part = p->split;
-    vp.split_cnt = p->ctl + 4;
-    vp.head = p->ctl;
+    vp.split_cnt = p->ctl + kCtlSplit;
+    vp.head = p->ctl + kCtlVarHead;
+    vp.exit_cnt = p->ctl + kCtlVarExit;
     vp.status = p->status;
-    GS_CUDA(cudaMemsetAsync(p->ctl, 0, sizeof(int32_t) * (4 + static_cast<size_t>(p->h.n_split) * c.n_chunks), s),
-            "memset counters");
     const int64_t total = static_cast<int64_t>(vp.n_items) * c.n_chunks;
     if (total > 0) {
         alignas(64) CUtensorMap tm;
@@ -782,9 +789,9 @@ gs_status gs_forward(gs_problem* p, const void* x, gs_dtype dtype, int32_t B, in
     fp.ctab = p->fctab;
     fp.x = x;
     fp.loss_part = p->part;
-    fp.head = p->ctl + 1;
+    fp.head = p->ctl + kCtlFwdHead;
+    fp.exit_cnt = p->ctl + kCtlFwdExit;
     fp.status = p->status;
-    GS_CUDA(cudaMemsetAsync(p->ctl + 1, 0, sizeof(int32_t), s), "memset head");
     const int64_t total = static_cast<int64_t>(fp.n_items) * c.n_chunks;
     if (total > 0) {
         const int grid = static_cast<int>(std::min<int64_t>(grid_forward(dtype, c.lc), total));
@@ -907,7 +914,11 @@ gs_status gs_sync_status(gs_problem* p) {
     GS_CUDA(cudaMemcpy(&h, p->status, sizeof(h), cudaMemcpyDeviceToHost), "read status");
     if (h) {
         GS_CUDA(cudaMemset(p->status, 0, sizeof(int32_t)), "clear status");
-        if (h & kStatusTimeout) return fail(GS_ERR_TIMEOUT, "a bounded device-side wait timed out");
+        if (h & kStatusTimeout) {
+            // a launch gave up part-way: its queue and split counters may not have been rewound
+            if (p->ctl) GS_CUDA(cudaMemset(p->ctl, 0, sizeof(int32_t) * p->ctl_cap), "clear counters");
+            return fail(GS_ERR_TIMEOUT, "a bounded device-side wait timed out");
+        }
         if (h & kStatusSelect) return fail(GS_ERR_STATE, "a pool selection found more rows than its rank");
     }
     return GS_OK;
@@ -979,6 +990,7 @@ extern "C" gs_status gs_forward_noalloc(gs_problem* p, const void* x, gs_dtype d
     unsigned char* base = nullptr;
     if ((st = noalloc_scratch(p->device, &base)) != GS_OK) return st;
     int32_t* head = reinterpret_cast<int32_t*>(base);
+    int32_t* exit_cnt = head + 1;
     float* part = reinterpret_cast<float*>(base + kNoAllocHeader);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     FwdParams fp{};
@@ -993,8 +1005,9 @@ extern "C" gs_status gs_forward_noalloc(gs_problem* p, const void* x, gs_dtype d
     fp.x = x;
     fp.loss_part = part;
     fp.head = head;
+    fp.exit_cnt = exit_cnt;
     fp.status = p->status;
-    GS_CUDA(cudaMemsetAsync(head, 0, sizeof(int32_t), s), "memset no-alloc counter");
+    GS_CUDA(cudaMemsetAsync(head, 0, 2 * sizeof(int32_t), s), "memset no-alloc counters");
     const int64_t total = static_cast<int64_t>(fp.n_items) * c.n_chunks;
     if (total > 0) {
         const int grid = static_cast<int>(std::min<int64_t>(grid_forward(dtype, c.lc), total));
@@ -1099,11 +1112,10 @@ gs_status gs_st_step(gs_problem* p, float* delta, float* m, float* v, const uint
     sp.adam = adam_consts(a, step);
     sp.split_part = p->split;
     sp.bpad = c.bpad;
-    sp.split_cnt = p->ctl + 4;
-    sp.head = p->ctl;
+    sp.split_cnt = p->ctl + kCtlSplit;
+    sp.head = p->ctl + kCtlVarHead;
+    sp.exit_cnt = p->ctl + kCtlVarExit;
     sp.status = p->status;
-    GS_CUDA(cudaMemsetAsync(p->ctl, 0, sizeof(int32_t) * (4 + static_cast<size_t>(p->h.n_split) * c.n_chunks), s),
-            "memset counters");
     const int64_t total = static_cast<int64_t>(sp.n_items) * c.n_chunks;
     if (total > 0) {
         const int grid = static_cast<int>(std::min<int64_t>(grid_st_pass(c.lw), total));

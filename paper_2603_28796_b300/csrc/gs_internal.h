@@ -140,8 +140,9 @@ struct VarParams {
     AdamK adam;
     float* loss_part;        // [n_items][bpad] or null
     float* split_part;       // [split rows][bpad]
-    int32_t* split_cnt;      // [n_split][n_chunks]
+    int32_t* split_cnt;      // [n_split][n_chunks], each cleared by the last part
     int32_t* head;
+    int32_t* exit_cnt;
     int32_t* status;
 };
 
@@ -174,8 +175,9 @@ struct StParams {
     AdamK adam;
     float* split_part;           // [split rows][bpad] partial integer gradients
     int32_t bpad;                // n_chunks * LW * 32
-    int32_t* split_cnt;          // [n_split][n_chunks]
+    int32_t* split_cnt;          // [n_split][n_chunks], each cleared by the last part
     int32_t* head;
+    int32_t* exit_cnt;
     int32_t* status;
 };
 
@@ -214,6 +216,7 @@ struct FwdParams {
     const void* x;
     float* loss_part;        // [n_items][bpad]
     int32_t* head;
+    int32_t* exit_cnt;
     int32_t* status;
 };
 
@@ -229,8 +232,17 @@ struct CheckParams {
     uint16_t* part16;        // [n_items][bpad16] per-tile unsat counts
     int32_t bpad16;          // nwd * 64
     int32_t* head;
+    int32_t* exit_cnt;
     int32_t* status;
 };
+
+// Work-queue control words (one int32 array per problem): heads and exit counts of the
+// variable-major, forward and check queues, then the split-variable part counters. All are zero
+// between launches (each kernel's last CTA rewinds its queue; the last part of a split variable
+// clears its counter); gs_sync_status clears them after a timed-out launch.
+constexpr int kCtlVarHead = 0, kCtlFwdHead = 1, kCtlCheckHead = 2;
+constexpr int kCtlVarExit = 3, kCtlFwdExit = 4, kCtlCheckExit = 5;
+constexpr int kCtlSplit = 8;
 
 // Device status bits (sticky until read by gs_sync_status).
 constexpr int32_t kStatusTimeout = 1;

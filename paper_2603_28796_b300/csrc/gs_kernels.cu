@@ -697,6 +697,7 @@ __device__ __forceinline__ void process_var_item(const VarParams& P, int w, cons
         if (lane == 0) prev = atomicAdd(&P.split_cnt[static_cast<int64_t>(it.split) * P.n_chunks + chunk], 1);
         prev = __shfl_sync(0xffffffffu, prev, 0);
         if (prev == it.n_parts - 1) {
+            if (lane == 0) P.split_cnt[static_cast<int64_t>(it.split) * P.n_chunks + chunk] = 0;   // rewind
             __threadfence();
             float ge[VPG];
 #pragma unroll
@@ -762,7 +763,7 @@ __global__ void __launch_bounds__(kThreads, Elem<T>::VEC == 4 ? 3 : 2) k_var_pas
                 if (wn < total) mbar_wait_bounded(&bars[buf ^ 1], phase[buf ^ 1], kWaitNs);
             }
             __syncwarp();
-            return;
+            break;
         }
         phase[buf] ^= 1u;
         process_var_item<T, MODE, LC>(P, w, wbase + buf * kVarBufBytes, g, li, lane);
@@ -770,6 +771,7 @@ __global__ void __launch_bounds__(kThreads, Elem<T>::VEC == 4 ? 3 : 2) k_var_pas
         w = wn;
         buf ^= 1;
     }
+    queue_exit(P.head, P.exit_cnt);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -922,6 +924,7 @@ __device__ __forceinline__ bool process_var_ring(const VarParams& P, const CUten
             if (lane == 0) prev = atomicAdd(&P.split_cnt[static_cast<int64_t>(it.split) * P.n_chunks + chunk], 1);
             prev = __shfl_sync(0xffffffffu, prev, 0);
             if (prev == it.n_parts - 1) {
+                if (lane == 0) P.split_cnt[static_cast<int64_t>(it.split) * P.n_chunks + chunk] = 0;   // rewind
                 __threadfence();
                 float ge[VPG];
 #pragma unroll
@@ -998,12 +1001,13 @@ __global__ void __launch_bounds__(kRingWarps * 32) k_var_ring(const VarParams P,
                 }
             }
             __syncwarp();
-            return;
+            break;
         }
         __syncwarp();
         w = wn;
         buf ^= 1;
     }
+    queue_exit(P.head, P.exit_cnt);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -1093,7 +1097,7 @@ __global__ void __launch_bounds__(kThreads) k_forward(const FwdParams P) {
                 if (wn < total) mbar_wait_bounded(&bars[buf ^ 1], phase[buf ^ 1], kWaitNs);
             }
             __syncwarp();
-            return;
+            break;
         }
         phase[buf] ^= 1u;
         {
@@ -1130,6 +1134,7 @@ __global__ void __launch_bounds__(kThreads) k_forward(const FwdParams P) {
         w = wn;
         buf ^= 1;
     }
+    queue_exit(P.head, P.exit_cnt);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -1173,7 +1178,7 @@ __global__ void __launch_bounds__(kThreads) k_check(const CheckParams P) {
                 if (wn < total) mbar_wait_bounded(&bars[buf ^ 1], phase[buf ^ 1], kWaitNs);
             }
             __syncwarp();
-            return;
+            break;
         }
         phase[buf] ^= 1u;
         {
@@ -1260,6 +1265,7 @@ __global__ void __launch_bounds__(kThreads) k_check(const CheckParams P) {
         w = wn;
         buf ^= 1;
     }
+    queue_exit(P.head, P.exit_cnt);
 }
 
 // ------------------------------------------------------------------------------------------

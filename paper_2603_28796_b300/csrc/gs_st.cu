@@ -303,6 +303,7 @@ __device__ __forceinline__ void process_st_item(const StParams& P, int w, const 
         if (lane == 0) prev = atomicAdd(&P.split_cnt[static_cast<int64_t>(it.split) * P.n_chunks + chunk], 1);
         prev = __shfl_sync(0xffffffffu, prev, 0);
         if (prev == it.n_parts - 1) {
+            if (lane == 0) P.split_cnt[static_cast<int64_t>(it.split) * P.n_chunks + chunk] = 0;   // rewind
             __threadfence();
             const float* rows = P.split_part + static_cast<int64_t>(it.split_row) * P.bpad + chunk * 32 * LW;
             st_epilogue<LW>(P, v, chunk, lane, [&](int, int, int base, float (&gx)[8]) {
@@ -354,7 +355,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_st_pass(const StParams P) {
                 if (wn < total) mbar_wait_bounded(&bars[buf ^ 1], phase[buf ^ 1], kWaitNs);
             }
             __syncwarp();
-            return;
+            break;
         }
         phase[buf] ^= 1u;
         process_st_item<LW>(P, w, wbase + buf * kVarBufBytes, g, li, lane);
@@ -362,6 +363,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_st_pass(const StParams P) {
         w = wn;
         buf ^= 1;
     }
+    queue_exit(P.head, P.exit_cnt);
 }
 
 // Logistic noise of one step, [n][ldB] float32: one thread per 8 candidates of a row.
