@@ -31,7 +31,9 @@ __device__ __forceinline__ void philox4x32_10(uint32_t (&x)[4], uint32_t k0, uin
 // k = top 23 bits of the word, u = (k + 1/2) 2^-23 (exact in float32), l = log(u / (1 - u)).
 __device__ __forceinline__ float logistic_from_word(uint32_t w) {
     const float u = (static_cast<float>(w >> 9) + 0.5f) * 0x1p-23f;
-    return logf(__fdiv_rn(u, 1.0f - u));
+    // fast log: documented error 2^-21.41 absolute on [0.5, 2] and 3 ulp elsewhere, below the
+    // spacing of the 23-bit draws (>= 4 * 2^-23 in l)
+    return __logf(__fdiv_rn(u, 1.0f - u));
 }
 
 }  // namespace

@@ -84,7 +84,7 @@ __device__ __forceinline__ void st_adam1(float gx, float l, float& d, float& m, 
     m = fmaf(k.beta1, m, k.one_minus_beta1 * g);
     v = fmaf(k.beta2, v, k.one_minus_beta2 * (g * g));
     const float den = sqrtf(v) * k.inv_sqrt_bc2 + k.eps;
-    d = d - k.step_size * (m * __frcp_rn(den));
+    d = d - k.step_size * __fdividef(m, den);   // den >= eps > 0
 }
 
 // ------------------------------------------------------------------------------------------

@@ -52,8 +52,12 @@ def problem(kind):
 
 
 def noise_bound(k23):
+    """|l_kernel - l| for l = log(u / (1 - u)): the correctly rounded quotient (2^-24 relative, so
+    2^-24 in l) and the fast log's documented error (2^-21.41 absolute near 1, 3 ulp elsewhere),
+    plus the final rounding."""
     u = (k23.astype(np.float64) + 0.5) / 2 ** 23
-    return 4 * U * (np.abs(np.log(u)) + np.abs(np.log1p(-u))) + 1e-12
+    l = np.abs(np.log(u) - np.log1p(-u))
+    return 2.0 ** -21.41 + 2.0 ** -24 + 4 * 2 * U * l + 1e-12
 
 
 @pytest.mark.parametrize("B", [1, 37, 64, 200])
