@@ -201,3 +201,53 @@ def test_precision_bf16_quantisation_error_bound():
     assert np.all(err <= bound), float((err / np.maximum(bound, 1e-300)).max())
     # and the error is far from vacuous: the relative L2 error is well below 1 %
     assert np.linalg.norm(err) / np.linalg.norm(g_ref) < 1e-2
+
+
+def test_differentiation_straight_through_step_sampled():
+    """The straight-through step at full size (n=100,000, B=1024) with explicit noise, on sampled
+    columns: hard assignments and unsat counts bit-exact, Adam within the derived bound."""
+    from tests.test_gpu_st import U
+    cnf, prob = workload("differentiation")
+    n, B, t = cnf.n_vars, 1024, 3
+    d0 = synth.init_delta(n, B, seed=301)
+    m0 = synth.normal_values(n, B, seed=302, scale=0.02)
+    v0 = np.abs(synth.normal_values(n, B, seed=303, scale=0.005))
+    l0 = oracle.logistic_noise(n, B, 304, t)[0].astype(np.float32)
+    l1 = oracle.logistic_noise(n, B, 304, t + 1)[0].astype(np.float32)
+    delta, m, v = (H.device_cands(a, B) for a in (d0, m0, v0))
+    bi = torch.zeros((n, B // 64), dtype=torch.int64, device="cuda")
+    bo = torch.zeros((n, B // 64), dtype=torch.int64, device="cuda")
+    _abi.gs_st_sample(prob, delta, bi, noise=H.device_cands(l0, B))
+    unsat = torch.zeros((1, B), dtype=torch.int32, device="cuda")
+    _abi.gs_check_bits(prob, bi, B, unsat)
+    _abi.gs_st_step(prob, delta, m, v, bi, bo, t, noise=H.device_cands(l0, B), noise_next=H.device_cands(l1, B))
+    torch.cuda.synchronize()
+    S = SAMPLE
+    ref = oracle.st_step(n, cnf.clause_ptr, cnf.lits, d0[:, S], m0[:, S], v0[:, S], l0[:, S], l1[:, S], t)
+    assert np.array_equal(unsat.cpu().numpy()[0][S], ref["unsat"])
+    assert np.array_equal(H.unpack_bits(bi, n, B)[:, S], ref["x_hat"])
+    z = d0[:, S].astype(np.float64) + l0[:, S].astype(np.float64)
+    z_err = 2 * U * (np.abs(d0[:, S]) + np.abs(l0[:, S]))
+    tol = H.adam_tolerances(d0[:, S], m0[:, S], v0[:, S], ref["grad"], 0.0, t, g_rel=0.0, z=z, z_err=z_err)
+    out = dict(delta=H.host64(delta)[:, S], m=H.host64(m)[:, S], v=H.host64(v)[:, S])
+    H.check_adam(out, ref, tol, "full-size straight-through step")
+    got = H.unpack_bits(bo, n, B)[:, S]
+    tie = np.abs(ref["delta"] + l1[:, S].astype(np.float64)) <= tol["delta"] + 1e-30
+    assert np.array_equal(got[~tie], ref["x_hat_next"][~tie])
+
+
+def test_differentiation_pool_full_size():
+    """Candidate pool on the full-size formula: N = 100 samples, S = 50, given noise: bit-exact."""
+    from paper_2603_28796_b300 import pool
+    cnf, prob = workload("differentiation")
+    n, B, N = cnf.n_vars, 1024, 100
+    S = pool.selection_size(n)
+    d = synth.init_delta(n, B, seed=305)
+    l = oracle.logistic_noise(n, N, 306, 0)[0].astype(np.float32)
+    bits, sel = _abi.gs_pool_sample(prob, H.device_cands(d, B), 700, N, S, noise=H.device_cands(l, N))
+    torch.cuda.synchronize()
+    x_ref, sel_ref = oracle.pool_select(d[:, 700], l, S)
+    assert np.array_equal(sel.cpu().numpy(), sel_ref)
+    assert np.array_equal(H.unpack_bits(bits, n, N).T, x_ref)
+    vars_ = _abi.gs_branch_vars(prob, H.device_cands(d, B), 700, 7).cpu().numpy()
+    assert np.array_equal(vars_, oracle.branch_select(d[:, 700], 7))
