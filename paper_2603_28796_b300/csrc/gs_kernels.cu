@@ -467,11 +467,13 @@ struct VarCfg {
     static constexpr int VEC = Elem<T>::VEC;
     static constexpr int G = 32 / LC;
     static constexpr int BC = LC * VEC;
-    static constexpr int NB = (VEC == 4) ? 8 : 4;
+    static constexpr int NB = 8;                                // gathers in flight per slot batch
     static constexpr int VPG = (VEC / G) > 0 ? (VEC / G) : 1;   // epilogue candidates per lane
     static constexpr int GE = VEC / VPG;                        // groups active in the epilogue
     static constexpr int N32 = BC >= 32 ? BC / 32 : 1;          // 32-bit bit-words per chunk
-    static constexpr bool PREFETCH = (VEC == 8);                // Adam state loaded before the gathers
+    // Adam state loaded before the gathers when each lane keeps few epilogue candidates (16-bit
+    // values in narrow chunks); with 32-lane chunks the registers go to the gathers instead
+    static constexpr bool PREFETCH = (VEC == 8) && (LC < 32);
 };
 
 // Adam state (delta, m, v) of the epilogue candidates of one lane.
