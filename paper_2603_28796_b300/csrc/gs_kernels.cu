@@ -1242,24 +1242,31 @@ __global__ void __launch_bounds__(kThreads) k_check(const CheckParams P) {
                     planes[p] = sum;
                 }
             }
-            if (g == 0 && ok_w) {
-                // 64 counts of this lane's word -> 32 uint32 pairs -> 8 vector stores
-                uint4* dst = reinterpret_cast<uint4*>(P.part16 + static_cast<int64_t>(item) * P.bpad16 + wd * 64);
+            if (ok_w) {
+                // every lane group now holds the word's totals: group g turns its 64 / G of the
+                // word's 64 counts into uint16 (pairs packed in uint32) and stores them
+                constexpr int PER = 64 / G;
+                const int c0 = g * PER;
+                uint16_t* dst16 = P.part16 + static_cast<int64_t>(item) * P.bpad16 + wd * 64 + c0;
+                auto pair = [&](int b0) -> uint32_t {
+                    uint32_t a = 0, b = 0;
 #pragma unroll
-                for (int q = 0; q < 8; ++q) {
-                    uint32_t wv[4];
-#pragma unroll
-                    for (int r = 0; r < 4; ++r) {
-                        const int b0 = q * 8 + r * 2;
-                        uint32_t c0 = 0, c1 = 0;
-#pragma unroll
-                        for (int p = 0; p < kPlanes; ++p) {
-                            c0 |= static_cast<uint32_t>((planes[p] >> b0) & 1ull) << p;
-                            c1 |= static_cast<uint32_t>((planes[p] >> (b0 + 1)) & 1ull) << p;
-                        }
-                        wv[r] = c0 | (c1 << 16);
+                    for (int p = 0; p < kPlanes; ++p) {
+                        a |= static_cast<uint32_t>((planes[p] >> b0) & 1ull) << p;
+                        b |= static_cast<uint32_t>((planes[p] >> (b0 + 1)) & 1ull) << p;
                     }
-                    dst[q] = make_uint4(wv[0], wv[1], wv[2], wv[3]);
+                    return a | (b << 16);
+                };
+                if constexpr (PER >= 8) {
+                    uint4* dst = reinterpret_cast<uint4*>(dst16);
+#pragma unroll
+                    for (int q = 0; q < PER / 8; ++q)
+                        dst[q] = make_uint4(pair(c0 + 8 * q), pair(c0 + 8 * q + 2), pair(c0 + 8 * q + 4),
+                                            pair(c0 + 8 * q + 6));
+                } else {
+                    uint32_t* dst = reinterpret_cast<uint32_t*>(dst16);
+#pragma unroll
+                    for (int q = 0; q < PER / 2; ++q) dst[q] = pair(c0 + 2 * q);
                 }
             }
         }
