@@ -173,6 +173,12 @@ gs_status gs_reserve(gs_problem* prob, int32_t B, gs_dtype dtype);
  *              (currently 1), 1 = credited inside the variable-major pass at each clause's first
  *              literal, 2 = a separate clause-major forward pass on x_in (fewer instructions in the
  *              variable pass; faster for wide clauses and small candidate rows).
+ *   var_split  how the lane groups of a warp share the variable-major pass when a candidate
+ *              chunk spans fewer than 32 lanes (small B): 0 = automatic (currently 1), 1 = all
+ *              groups work on one variable at a time, splitting its occurrences (tiles staged in
+ *              shared memory by TMA), 2 = each group owns whole variables of a run of variables
+ *              cut at equal code counts (codes read from global memory; no per-variable
+ *              reduction across groups, less padding of the gather batches).
  * Results do not depend on the tuning beyond float32 summation order. Call gs_reserve again
  * after changing it if later calls are captured in a CUDA graph.
  */
@@ -181,6 +187,7 @@ typedef struct {
     int32_t fwd_lanes;
     int32_t var_gather;
     int32_t loss_mode;
+    int32_t var_split;
 } gs_tuning;
 
 /* gs_set_tuning / gs_get_tuning - set or read the caps above. Errors: GS_ERR_INVALID_ARG. */

@@ -56,11 +56,12 @@ class GsInfo(ctypes.Structure):
 
 class GsTuning(ctypes.Structure):
     _fields_ = [("var_lanes", ctypes.c_int32), ("fwd_lanes", ctypes.c_int32), ("var_gather", ctypes.c_int32),
-                ("loss_mode", ctypes.c_int32)]
+                ("loss_mode", ctypes.c_int32), ("var_split", ctypes.c_int32)]
 
     def as_dict(self) -> dict:
         return {"var_lanes": int(self.var_lanes), "fwd_lanes": int(self.fwd_lanes),
-                "var_gather": int(self.var_gather), "loss_mode": int(self.loss_mode)}
+                "var_gather": int(self.var_gather), "loss_mode": int(self.loss_mode),
+                "var_split": int(self.var_split)}
 
 
 class GsAdam(ctypes.Structure):
@@ -284,8 +285,8 @@ def gs_info_get(prob: Problem) -> dict:
 
 
 def gs_set_tuning(prob: Problem, var_lanes: int = 0, fwd_lanes: int = 0, var_gather: int = 0,
-                  loss_mode: int = 0) -> None:
-    t = GsTuning(int(var_lanes), int(fwd_lanes), int(var_gather), int(loss_mode))
+                  loss_mode: int = 0, var_split: int = 0) -> None:
+    t = GsTuning(int(var_lanes), int(fwd_lanes), int(var_gather), int(loss_mode), int(var_split))
     _check(lib().gs_set_tuning(prob.handle, ctypes.byref(t)), "gs_set_tuning")
 
 

@@ -63,6 +63,9 @@ Chunking chunking_for(int dtype, int32_t B, int lc_max = 32) {
     const int need = (B + c.vec - 1) / c.vec;
     c.lc = 4;
     while (c.lc < need && c.lc < lc_max) c.lc *= 2;
+    // The variable pass writes the rounded bits as whole 32-bit words per chunk, so a chunk of
+    // fewer than 32 candidates is only allowed when it is the only one.
+    if (c.lc * c.vec < 32 && c.lc < need) c.lc = 32 / c.vec;
     c.bc = c.lc * c.vec;
     c.n_chunks = (B + c.bc - 1) / c.bc;
     if (c.n_chunks < 1) c.n_chunks = 1;
@@ -90,8 +93,12 @@ struct gs_problem {
     int32_t* f_list = nullptr;
     int32_t* v_iptr = nullptr;
     int32_t* v_list = nullptr;
+    uint32_t* otab = nullptr;    // variable-owned items (lane groups own whole variables)
+    VarItem* oitems = nullptr;
+    int32_t* o_iptr = nullptr;
+    int32_t* o_list = nullptr;
     int64_t* inst_empty = nullptr;
-    int32_t n_fitems = 0, n_vitems = 0;
+    int32_t n_fitems = 0, n_vitems = 0, n_oitems = 0;
     int64_t n_vcodes = 0;
     int32_t* status = nullptr;   // sticky device status word
     // workspace
@@ -115,6 +122,7 @@ struct gs_problem {
     int fwd_lc_max = 32;
     int var_gather = 0;
     int loss_mode = 0;
+    int var_split = 0;
 };
 
 namespace {
@@ -175,7 +183,7 @@ gs_status ensure_ws(gs_problem* p, int dtype, int32_t B, bool need_bits, cudaStr
     const bool cap = capturing(s);
     const Chunking cv = chunking_for(dtype, B, p->var_lc_max);
     const Chunking cf = chunking_for(dtype, B, p->fwd_lc_max);
-    const size_t items = static_cast<size_t>(std::max(p->n_fitems, p->n_vitems));
+    const size_t items = static_cast<size_t>(std::max(p->n_fitems, std::max(p->n_vitems, p->n_oitems)));
     const size_t bpad = static_cast<size_t>(std::max(cv.bpad, cf.bpad));
     gs_status st;
     if ((st = grow(&p->part, &p->part_cap, std::max<size_t>(1, items * bpad), s, cap, "loss partials")) != GS_OK)
@@ -264,6 +272,7 @@ gs_status load(int32_t n_inst, const int64_t* n_vars, const int64_t* n_clauses, 
     HostPlan& H = p->h;
     p->n_fitems = static_cast<int32_t>(H.fitems.size());
     p->n_vitems = static_cast<int32_t>(H.vitems.size());
+    p->n_oitems = static_cast<int32_t>(H.oitems.size());
     p->n_vcodes = static_cast<int64_t>(H.vcodes.size());
     int64_t& db = p->device_bytes;
     if ((st = upload(H.fcodes, &p->fcodes, &db, s)) != GS_OK || (st = upload(H.fctab, &p->fctab, &db, s)) != GS_OK ||
@@ -271,7 +280,9 @@ gs_status load(int32_t n_inst, const int64_t* n_vars, const int64_t* n_clauses, 
         (st = upload(H.vrecs, &p->vrecs, &db, s)) != GS_OK || (st = upload(H.vtab, &p->vtab, &db, s)) != GS_OK ||
         (st = upload(H.vitems, &p->vitems, &db, s)) != GS_OK || (st = upload(H.f_iptr, &p->f_iptr, &db, s)) != GS_OK ||
         (st = upload(H.f_list, &p->f_list, &db, s)) != GS_OK || (st = upload(H.v_iptr, &p->v_iptr, &db, s)) != GS_OK ||
-        (st = upload(H.v_list, &p->v_list, &db, s)) != GS_OK ||
+        (st = upload(H.v_list, &p->v_list, &db, s)) != GS_OK || (st = upload(H.otab, &p->otab, &db, s)) != GS_OK ||
+        (st = upload(H.oitems, &p->oitems, &db, s)) != GS_OK || (st = upload(H.o_iptr, &p->o_iptr, &db, s)) != GS_OK ||
+        (st = upload(H.o_list, &p->o_list, &db, s)) != GS_OK ||
         (st = upload(H.inst_empty, &p->inst_empty, &db, s)) != GS_OK) {
         gs_free(p);
         return st;
@@ -294,6 +305,8 @@ gs_status load(int32_t n_inst, const int64_t* n_vars, const int64_t* n_clauses, 
     std::vector<uint16_t>().swap(H.vrecs);
     std::vector<uint32_t>().swap(H.vtab);
     std::vector<VarItem>().swap(H.vitems);
+    std::vector<uint32_t>().swap(H.otab);
+    std::vector<VarItem>().swap(H.oitems);
     *out = p;
     return GS_OK;
 }
@@ -440,10 +453,20 @@ gs_status var_pass(gs_problem* p, int mode, const void* x_in, int dtype, int32_t
     vp.head = p->ctl + kCtlVarHead;
     vp.exit_cnt = p->ctl + kCtlVarExit;
     vp.status = p->status;
+    // lane groups own whole variables (var_split 2) when a chunk leaves more than one group
+    const bool own = p->var_split == 2 && c.lc < 32 && p->h.own_ok;
+    if (own) {
+        vp.items = p->oitems;
+        vp.n_items = p->n_oitems;
+        vp.vtab = p->otab;
+    }
     const int64_t total = static_cast<int64_t>(vp.n_items) * c.n_chunks;
     if (total > 0) {
         alignas(64) CUtensorMap tm;
-        if (c.lc == 32 && p->var_gather == 2 && encode_rows_map(&tm, x_in, dtype, p->h.n, B, ldB)) {
+        if (own) {
+            const int grid = static_cast<int>(std::min<int64_t>(grid_var_own(dtype, mode, c.lc), total));
+            GS_CUDA(launch_var_own(vp, dtype, mode, c.lc, grid, s), "variable pass (owned variables) launch");
+        } else if (c.lc == 32 && p->var_gather == 2 && encode_rows_map(&tm, x_in, dtype, p->h.n, B, ldB)) {
             const int grid = static_cast<int>(std::min<int64_t>(grid_var_ring(dtype, mode), total));
             GS_CUDA(launch_var_ring(vp, &tm, dtype, mode, grid, s), "variable pass (TMA gather) launch");
         } else {
@@ -452,8 +475,8 @@ gs_status var_pass(gs_problem* p, int mode, const void* x_in, int dtype, int32_t
         }
     }
     if (loss)
-        GS_CUDA(launch_loss_reduce2(p->part, c.bpad, p->v_iptr, p->v_list, p->inst_empty, p->h.n_inst, B,
-                                    n_segments(p, B), p->stage, loss, s),
+        GS_CUDA(launch_loss_reduce2(p->part, c.bpad, own ? p->o_iptr : p->v_iptr, own ? p->o_list : p->v_list,
+                                    p->inst_empty, p->h.n_inst, B, n_segments(p, B), p->stage, loss, s),
                 "loss reduce launch");
     return GS_OK;
 }
@@ -589,10 +612,12 @@ gs_status gs_set_tuning(gs_problem* p, const gs_tuning* t) {
         return fail(GS_ERR_INVALID_ARG, "lanes per candidate chunk must be 0, 4, 8, 16 or 32");
     if (t->var_gather < 0 || t->var_gather > 2) return fail(GS_ERR_INVALID_ARG, "var_gather must be 0, 1 or 2");
     if (t->loss_mode < 0 || t->loss_mode > 2) return fail(GS_ERR_INVALID_ARG, "loss_mode must be 0, 1 or 2");
+    if (t->var_split < 0 || t->var_split > 2) return fail(GS_ERR_INVALID_ARG, "var_split must be 0, 1 or 2");
     p->var_lc_max = t->var_lanes ? t->var_lanes : 32;
     p->fwd_lc_max = t->fwd_lanes ? t->fwd_lanes : 32;
     p->var_gather = t->var_gather;
     p->loss_mode = t->loss_mode;
+    p->var_split = t->var_split;
     return GS_OK;
 }
 
@@ -602,6 +627,7 @@ gs_status gs_get_tuning(const gs_problem* p, gs_tuning* t) {
     t->fwd_lanes = p->fwd_lc_max;
     t->var_gather = p->var_gather;
     t->loss_mode = p->loss_mode;
+    t->var_split = p->var_split;
     return GS_OK;
 }
 
@@ -639,7 +665,7 @@ gs_status gs_autotune(gs_problem* p, int32_t B, gs_dtype dtype, gs_stream stream
         cleanup();
         return fail(GS_ERR_CUDA, "gs_autotune memset");
     }
-    const gs_tuning saved{p->var_lc_max, p->fwd_lc_max, p->var_gather, p->loss_mode};
+    const gs_tuning saved{p->var_lc_max, p->fwd_lc_max, p->var_gather, p->loss_mode, p->var_split};
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
@@ -665,10 +691,15 @@ gs_status gs_autotune(gs_problem* p, int32_t B, gs_dtype dtype, gs_stream stream
         const int lc = chunking_for(dtype, B, lanes).lc;
         if (tried & lc) continue;
         tried |= lc;
-        for (int gather = 1; gather <= 2; ++gather) {
-            if (gather == 2 && lc != 32) continue;
+        // (gather, split): register loads with shared variables, the TMA ring (32-lane chunks),
+        // variable-owning lane groups (narrower chunks)
+        const int forms[3][2] = {{1, 1}, {2, 1}, {1, 2}};
+        for (const auto& f : forms) {
+            if (f[0] == 2 && lc != 32) continue;
+            if (f[1] == 2 && (lc == 32 || !p->h.own_ok)) continue;
             p->var_lc_max = lanes;
-            p->var_gather = gather;
+            p->var_gather = f[0];
+            p->var_split = f[1];
             if ((rs = ensure_ws(p, dtype, B, false, s)) != GS_OK) break;
             const float ms = timed([&] {
                 return gs_step(p, delta, m, v, nullptr, x0, x1, dtype, B, ldB, ++step, nullptr, loss, nullptr, stream);
@@ -676,7 +707,8 @@ gs_status gs_autotune(gs_problem* p, int32_t B, gs_dtype dtype, gs_stream stream
             if (ms > 0.0f && (best_ms < 0.0f || ms < best_ms)) {
                 best_ms = ms;
                 best.var_lanes = lanes;
-                best.var_gather = gather;
+                best.var_gather = f[0];
+                best.var_split = f[1];
             }
         }
     }
@@ -699,6 +731,7 @@ gs_status gs_autotune(gs_problem* p, int32_t B, gs_dtype dtype, gs_stream stream
     if (rs == GS_OK) {
         p->var_lc_max = best.var_lanes;
         p->var_gather = best.var_gather;
+        p->var_split = best.var_split;
         p->fwd_lc_max = best.fwd_lanes;
         float mode_ms[3] = {-1.0f, -1.0f, -1.0f};
         for (int mode = 1; mode <= 2 && rs == GS_OK; ++mode) {
@@ -718,6 +751,7 @@ gs_status gs_autotune(gs_problem* p, int32_t B, gs_dtype dtype, gs_stream stream
     p->fwd_lc_max = saved.fwd_lanes;
     p->var_gather = saved.var_gather;
     p->loss_mode = saved.loss_mode;
+    p->var_split = saved.var_split;
     if (rs != GS_OK) return rs;
     if (se != cudaSuccess) return cuda_fail(se, "gs_autotune");
     if ((st = gs_set_tuning(p, &best)) != GS_OK) return st;
@@ -740,6 +774,10 @@ gs_status gs_reserve(gs_problem* p, int32_t B, gs_dtype dtype) {
     grid_var_pass(dtype, kModeAdam, cv.lc);
     grid_var_ring(dtype, kModeGrad);
     grid_var_ring(dtype, kModeAdam);
+    if (cv.lc < 32) {
+        grid_var_own(dtype, kModeGrad, cv.lc);
+        grid_var_own(dtype, kModeAdam, cv.lc);
+    }
     tensor_map_encoder();
     grid_forward(dtype, cf.lc);
     grid_check(lanes_for_words(nwords(B)));
@@ -928,9 +966,10 @@ void gs_free(gs_problem* p) {
     if (!p) return;
     int dev = -1;
     if (cudaGetDevice(&dev) == cudaSuccess && dev == p->device) cudaDeviceSynchronize();
-    void* ptrs[] = {p->fcodes, p->fctab,  p->fitems,     p->vcodes, p->vrecs, p->vtab,  p->vitems,
-                    p->f_iptr, p->f_list, p->v_iptr,     p->v_list, p->inst_empty, p->status, p->ctl,
-                    p->part,   p->split,  p->bits,       p->part16, p->stage, p->pool};
+    void* ptrs[] = {p->fcodes, p->fctab,  p->fitems, p->vcodes,     p->vrecs,  p->vtab,   p->vitems,
+                    p->f_iptr, p->f_list, p->v_iptr, p->v_list,     p->otab,   p->oitems, p->o_iptr,
+                    p->o_list, p->status, p->ctl,    p->inst_empty, p->part,   p->split,  p->bits,
+                    p->part16, p->stage,  p->pool};
     for (void* q : ptrs)
         if (q) cudaFree(q);
     delete p;

@@ -18,6 +18,8 @@ constexpr int kFwdClauses = 256;   // clauses per tile
 // whose occurrence list alone exceeds kVarCodes.
 constexpr int kVarCodes = 384;     // occurrence codes per tile
 constexpr int kVarVars = 64;       // variables per tile
+constexpr int kOwnCodes = 4096;    // codes per variable-owned item (whole variables; at least one)
+constexpr int kOwnVars = 1024;     // variables per variable-owned item
 
 constexpr int align16(int x) { return (x + 15) & ~15; }
 
@@ -253,6 +255,10 @@ constexpr int32_t kStatusSelect = 2;   // a selection found more rows than its r
 cudaError_t launch_var_pass(const VarParams& p, int dtype, int mode, int lc, int grid, cudaStream_t s);
 // tmap: a CUtensorMap (128 bytes) over x_in as a 2-D tensor [n rows][B columns], box {32*VEC, 1}.
 cudaError_t launch_var_ring(const VarParams& p, const void* tmap, int dtype, int mode, int grid, cudaStream_t s);
+// Variable pass with variable-owning lane groups (lc = 4, 8 or 16 lanes per chunk): items and
+// vtab of p are the own-item table (whole variables, nv + 1 relative code offsets per item).
+cudaError_t launch_var_own(const VarParams& p, int dtype, int mode, int lc, int grid, cudaStream_t s);
+int grid_var_own(int dtype, int mode, int lc);
 int grid_var_ring(int dtype, int mode);
 cudaError_t launch_forward(const FwdParams& p, int dtype, int lc, int grid, cudaStream_t s);
 cudaError_t launch_check(const CheckParams& p, int lw, int grid, cudaStream_t s);

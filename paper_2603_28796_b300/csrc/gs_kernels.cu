@@ -297,6 +297,14 @@ __device__ __forceinline__ uint4 load_row(const RowView& rv, uint32_t u) {
     return ld_gather16(rv.base + static_cast<uint64_t>(u) * rv.row_bytes);
 }
 
+template <bool GC>
+__device__ __forceinline__ uint32_t ld_code(const uint32_t* cd, int i) {
+    if constexpr (GC)
+        return __ldg(cd + i);
+    else
+        return cd[i];
+}
+
 // Loss credits of one variable's occurrences: the clause value U_t = f_own * LOO is credited at
 // the clause's position-0 literal. f_own is the variable's own factor, so the credits are summed
 // separately for positive (Cp) and negated (Cn) own literals and multiplied by 1 - x resp. x once,
@@ -309,7 +317,7 @@ struct Credits {
 // General slot loop over the occurrence codes [cs, ce) of the group, NB codes per batch; an
 // occurrence ends at a code carrying kVEnd. R is the running leave-one-out product (prefix then
 // suffix of the occurrence's clause), restarted after each end.
-template <typename T, int VEC, int NB, bool LOSS>
+template <typename T, int VEC, int NB, bool LOSS, bool GC>
 __device__ __forceinline__ void var_slots(const uint32_t* cd, int cs, int ce, const RowView& rv, float2 (&G2)[VEC / 2],
                                           Credits<VEC / 2>& cr) {
     constexpr int H = VEC / 2;
@@ -320,7 +328,7 @@ __device__ __forceinline__ void var_slots(const uint32_t* cd, int cs, int ce, co
         uint32_t cw[NB];
         uint4 raw[NB];
 #pragma unroll
-        for (int j = 0; j < NB; ++j) cw[j] = (s + j < ce) ? cd[s + j] : (kVSentinel << kVShift);
+        for (int j = 0; j < NB; ++j) cw[j] = (s + j < ce) ? ld_code<GC>(cd, s + j) : (kVSentinel << kVShift);
 #pragma unroll
         for (int j = 0; j < NB; ++j) {
             const uint32_t u = cw[j] >> kVShift;
@@ -373,7 +381,7 @@ __device__ __forceinline__ void fixed_ab(uint32_t c, float& a, float& b) {
     }
 }
 
-template <typename T, int VEC, int K, int OB, bool LOSS, bool TAIL>
+template <typename T, int VEC, int K, int OB, bool LOSS, bool TAIL, bool GC>
 __device__ __forceinline__ void occ_batch(const uint32_t* cd, int s, int ce, const RowView& rv, float2 (&G2)[VEC / 2],
                                           Credits<VEC / 2>& cr) {
     constexpr int H = VEC / 2;
@@ -381,7 +389,7 @@ __device__ __forceinline__ void occ_batch(const uint32_t* cd, int s, int ce, con
     uint32_t cw[NS];
     uint4 raw[NS];
 #pragma unroll
-    for (int j = 0; j < NS; ++j) cw[j] = (!TAIL || s + j < ce) ? cd[s + j] : (kVSentinel << kVShift);
+    for (int j = 0; j < NS; ++j) cw[j] = (!TAIL || s + j < ce) ? ld_code<GC>(cd, s + j) : (kVSentinel << kVShift);
 #pragma unroll
     for (int j = 0; j < NS; ++j) {
         raw[j] = make_uint4(0u, 0u, 0u, 0u);
@@ -419,18 +427,19 @@ __device__ __forceinline__ void occ_batch(const uint32_t* cd, int s, int ce, con
     }
 }
 
-template <typename T, int VEC, int K, bool LOSS>
+template <typename T, int VEC, int K, bool LOSS, bool GC>
 __device__ __forceinline__ void var_occ_fixed(const uint32_t* cd, int cs, int ce, const RowView& rv,
                                               float2 (&G2)[VEC / 2], Credits<VEC / 2>& cr) {
     constexpr int OB = (K == 1) ? 8 : (K == 2 ? 4 : 3);
     constexpr int NS = OB * K;
     int s = cs;
-    for (; s + NS <= ce; s += NS) occ_batch<T, VEC, K, OB, LOSS, false>(cd, s, ce, rv, G2, cr);
-    if (s < ce) occ_batch<T, VEC, K, OB, LOSS, true>(cd, s, ce, rv, G2, cr);
+    for (; s + NS <= ce; s += NS) occ_batch<T, VEC, K, OB, LOSS, false, GC>(cd, s, ce, rv, G2, cr);
+    if (s < ce) occ_batch<T, VEC, K, OB, LOSS, true, GC>(cd, s, ce, rv, G2, cr);
 }
 
-// Gradient and (with LOSS) loss credits of one variable's occurrence codes [cs, ce).
-template <typename T, int VEC, int NB, bool LOSS>
+// Gradient and (with LOSS) loss credits of one variable's occurrence codes [cs, ce); GC: the
+// codes are read from global memory instead of a shared-memory tile.
+template <typename T, int VEC, int NB, bool LOSS, bool GC = false>
 __device__ __forceinline__ void var_gather(int kk, const uint32_t* cd, int cs, int ce, const RowView& rv,
                                            float (&gacc)[VEC], Credits<VEC / 2>& cr) {
     constexpr int H = VEC / 2;
@@ -438,10 +447,10 @@ __device__ __forceinline__ void var_gather(int kk, const uint32_t* cd, int cs, i
 #pragma unroll
     for (int h = 0; h < H; ++h) G2[h] = dup2(0.0f);
     switch (kk) {
-        case 1: var_occ_fixed<T, VEC, 1, LOSS>(cd, cs, ce, rv, G2, cr); break;
-        case 2: var_occ_fixed<T, VEC, 2, LOSS>(cd, cs, ce, rv, G2, cr); break;
-        case 3: var_occ_fixed<T, VEC, 3, LOSS>(cd, cs, ce, rv, G2, cr); break;
-        default: var_slots<T, VEC, NB, LOSS>(cd, cs, ce, rv, G2, cr); break;
+        case 1: var_occ_fixed<T, VEC, 1, LOSS, GC>(cd, cs, ce, rv, G2, cr); break;
+        case 2: var_occ_fixed<T, VEC, 2, LOSS, GC>(cd, cs, ce, rv, G2, cr); break;
+        case 3: var_occ_fixed<T, VEC, 3, LOSS, GC>(cd, cs, ce, rv, G2, cr); break;
+        default: var_slots<T, VEC, NB, LOSS, GC>(cd, cs, ce, rv, G2, cr); break;
     }
 #pragma unroll
     for (int h = 0; h < H; ++h) {
@@ -772,6 +781,188 @@ __global__ void __launch_bounds__(kThreads, Elem<T>::VEC == 4 ? 3 : 2) k_var_pas
         __syncwarp();
         w = wn;
         buf ^= 1;
+    }
+    queue_exit(P.head, P.exit_cnt);
+}
+
+// ------------------------------------------------------------------------------------------
+// Variable-major pass with variable-owning lane groups (chunks of LC < 32 lanes). The same
+// arithmetic as k_var_pass, organised for small candidate rows: a work item is a run of whole
+// variables of about a few thousand codes, and each of the G = 32 / LC lane groups of the warp
+// takes a contiguous share of its variables (cut where the codes reach g / G of the item) and
+// runs each of them start to end: occurrence loop, gradient, epilogue. No group splits a
+// variable, so nothing is reduced across groups per variable and a group's batches of gathers
+// are only padded at the end of each of its variables. The codes are read straight from global
+// memory (each group reads its own contiguous run; consecutive batches share cache lines).
+template <typename T, int MODE, int LC>
+__device__ __forceinline__ void own_epilogue(const VarParams& P, int v, int inst, int chunk, int li, uint32_t gmask,
+                                             const float (&ge)[Elem<T>::VEC], const AdamState<Elem<T>::VEC>& st) {
+    constexpr int VEC = Elem<T>::VEC;
+    constexpr int BC = LC * VEC;
+    const int c0 = chunk * BC + li * VEC;
+    const bool act = c0 < P.B;
+    const bool full = c0 + VEC <= P.B;
+    const int64_t off = static_cast<int64_t>(v) * P.ldB + c0;
+    if constexpr (MODE == kModeGrad) {
+        if (act) {
+            float out[VEC];
+#pragma unroll
+            for (int el = 0; el < VEC; ++el) {
+                const float s = (P.dloss && c0 + el < P.B)
+                                    ? static_cast<float>(P.dloss[static_cast<int64_t>(inst) * P.B + c0 + el])
+                                    : 1.0f;
+                out[el] = ge[el] * s;
+            }
+            if (full) {
+                st_stream<VEC>(P.grad + off, out);
+            } else {
+                for (int el = 0; el < VEC && c0 + el < P.B; ++el) P.grad[off + el] = out[el];
+            }
+        }
+    } else {
+        uint32_t mybits = 0;
+        if (act) {
+            float d[VEC], mm[VEC], vv[VEC], xn[VEC];
+#pragma unroll
+            for (int el = 0; el < VEC; ++el) {
+                d[el] = st.d[el];
+                mm[el] = st.m[el];
+                vv[el] = st.v[el];
+            }
+#pragma unroll
+            for (int el = 0; el < VEC; ++el) {
+                adam_update(ge[el], d[el], mm[el], vv[el], xn[el], P.adam);
+                if (c0 + el < P.B && d[el] > 0.0f) mybits |= 1u << el;
+            }
+            T* xo = static_cast<T*>(P.x_out) + off;
+            if (full) {
+                st_stream<VEC>(P.delta + off, d);
+                st_stream<VEC>(P.m + off, mm);
+                st_stream<VEC>(P.v + off, vv);
+                st_vals<T, VEC>(xo, xn);
+            } else {
+                for (int el = 0; el < VEC && c0 + el < P.B; ++el) {
+                    P.delta[off + el] = d[el];
+                    P.m[off + el] = mm[el];
+                    P.v[off + el] = vv[el];
+                    xo[el] = from_f32<T>(xn[el]);
+                }
+            }
+        }
+        if (P.bits32) {
+            // lanes whose candidates share a 32-bit word OR their bits together (within the group)
+            constexpr int LPW = (32 / VEC) < LC ? (32 / VEC) : LC;
+            uint32_t word = mybits << (c0 & 31);
+#pragma unroll
+            for (int o = 1; o < LPW; o <<= 1) word |= __shfl_xor_sync(gmask, word, o);
+            const int64_t row = static_cast<int64_t>(v) * 2 * P.nwd;
+            const int hw = c0 >> 5;
+            if (li % LPW == 0 && hw < 2 * P.nwd) P.bits32[row + hw] = word;
+            if (li == 0 && chunk == P.n_chunks - 1) {
+                for (int z = (P.n_chunks * BC + 31) >> 5; z < 2 * P.nwd; ++z) P.bits32[row + z] = 0u;
+            }
+        }
+    }
+}
+
+template <typename T, int MODE, int LC>
+__device__ __forceinline__ void process_own_item(const VarParams& P, int w, int g, int li, int lane) {
+    constexpr int VEC = Elem<T>::VEC, G = 32 / LC, H = VEC / 2, BC = LC * VEC;
+    constexpr int NB = VarCfg<T, MODE, LC>::NB;
+    const int item = w % P.n_items;
+    const int chunk = w / P.n_items;
+    const VarItem it = P.items[item];
+    const uint32_t* tab = P.vtab + it.vtab_base;   // nv + 1 code offsets, relative to code_base
+    const uint32_t* cd = P.codes + it.code_base;
+    // group g owns variables [va, vb): the first variable whose codes start at or after
+    // n_codes * g / G opens its share; the last group takes everything to the end
+    auto share_start = [&](int gg) -> int {
+        if (gg >= G) return it.nv;
+        const uint32_t target = static_cast<uint32_t>((static_cast<int64_t>(it.n_codes) * gg) / G);
+        int lo = 0, hi = it.nv;
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (__ldg(tab + mid) < target)
+                lo = mid + 1;
+            else
+                hi = mid;
+        }
+        return lo;
+    };
+    const int va = share_start(g), vb = share_start(g + 1);
+    const uint32_t gmask = (LC == 32) ? 0xffffffffu : (((1u << LC) - 1u) << (g * LC));
+    const int lane_base = chunk * BC + li * VEC;
+    const bool ld_ok = lane_base < P.B;
+    RowView rv;
+    rv.base = reinterpret_cast<const char*>(static_cast<const T*>(P.x_in) + lane_base);
+    rv.row_bytes = static_cast<uint32_t>(P.ldB * sizeof(T));
+    rv.ok = ld_ok;
+    const bool loss = P.loss_part != nullptr;
+
+    float Ls[VEC], Lc[VEC];
+#pragma unroll
+    for (int e = 0; e < VEC; ++e) Ls[e] = Lc[e] = 0.0f;
+    int cs = (va < vb) ? static_cast<int>(__ldg(tab + va)) : 0;
+    for (int vi = va; vi < vb; ++vi) {
+        const int ce = static_cast<int>(__ldg(tab + vi + 1));
+        const int v = it.v0 + vi;
+        float gacc[VEC];
+        Credits<H> cr;
+#pragma unroll
+        for (int h = 0; h < H; ++h) cr.p[h] = cr.n[h] = dup2(0.0f);
+        if (loss) {
+            var_gather<T, VEC, NB, true, true>(it.kk, cd, cs, ce, rv, gacc, cr);
+            float xs[VEC];
+#pragma unroll
+            for (int e = 0; e < VEC; ++e) xs[e] = 0.0f;
+            if (ld_ok) unpack<T>(load_row(rv, static_cast<uint32_t>(v)), xs);
+            credit_flush<VEC>(cr, xs, Ls, Lc);
+        } else {
+            var_gather<T, VEC, NB, false, true>(it.kk, cd, cs, ce, rv, gacc, cr);
+        }
+        AdamState<VEC> st;
+        if constexpr (MODE == kModeAdam) {
+            const int64_t off = static_cast<int64_t>(v) * P.ldB + lane_base;
+            if (ld_ok && lane_base + VEC <= P.B) {
+                ld_stream<VEC>(P.delta + off, st.d);
+                ld_stream<VEC>(P.m + off, st.m);
+                ld_stream<VEC>(P.v + off, st.v);
+            } else {
+#pragma unroll
+                for (int el = 0; el < VEC; ++el) {
+                    const bool ok = lane_base + el < P.B;
+                    st.d[el] = ok ? P.delta[off + el] : 0.0f;
+                    st.m[el] = ok ? P.m[off + el] : 0.0f;
+                    st.v[el] = ok ? P.v[off + el] : 0.0f;
+                }
+            }
+        }
+        own_epilogue<T, MODE, LC>(P, v, it.inst, chunk, li, gmask, gacc, st);
+        cs = ce;
+    }
+    __syncwarp();
+    if (loss) {
+        float lf[VEC];
+#pragma unroll
+        for (int e = 0; e < VEC; ++e) lf[e] = Ls[e] - Lc[e];
+        group_sum<LC>(lf);
+        if (g == 0) {
+            float* dst = P.loss_part + static_cast<int64_t>(item) * P.bpad + lane_base;
+#pragma unroll
+            for (int e = 0; e < VEC; e += 4)
+                __stcg(reinterpret_cast<float4*>(dst + e), make_float4(lf[e], lf[e + 1], lf[e + 2], lf[e + 3]));
+        }
+    }
+}
+
+template <typename T, int MODE, int LC>
+__global__ void __launch_bounds__(kThreads, Elem<T>::VEC == 4 ? 3 : 2) k_var_own(const VarParams P) {
+    const int lane = threadIdx.x & 31;
+    const int g = lane / LC, li = lane % LC;
+    const int total = P.n_items * P.n_chunks;
+    for (int w = fetch_work(P.head, lane); w < total; w = fetch_work(P.head, lane)) {
+        process_own_item<T, MODE, LC>(P, w, g, li, lane);
+        __syncwarp();
     }
     queue_exit(P.head, P.exit_cnt);
 }
@@ -1472,6 +1663,37 @@ int check_grid_t() {
     return grid;
 }
 
+template <typename T, int MODE, int LC>
+int own_grid_t() {
+    static int grid = 0;
+    if (!grid) {
+        auto kernel = k_var_own<T, MODE, LC>;
+        cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxL1);
+        int per_sm = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kThreads, 0) != cudaSuccess || per_sm < 1)
+            per_sm = 1;
+        grid = per_sm * sm_count();
+    }
+    return grid;
+}
+template <typename T, int MODE>
+int own_grid_lc(int lc) {
+    switch (lc) {
+        case 16: return own_grid_t<T, MODE, 16>();
+        case 8: return own_grid_t<T, MODE, 8>();
+        default: return own_grid_t<T, MODE, 4>();
+    }
+}
+template <typename T, int MODE>
+cudaError_t own_launch_lc(const VarParams& p, int lc, int grid, cudaStream_t s) {
+    switch (lc) {
+        case 16: own_grid_t<T, MODE, 16>(); k_var_own<T, MODE, 16><<<grid, kThreads, 0, s>>>(p); break;
+        case 8: own_grid_t<T, MODE, 8>(); k_var_own<T, MODE, 8><<<grid, kThreads, 0, s>>>(p); break;
+        default: own_grid_t<T, MODE, 4>(); k_var_own<T, MODE, 4><<<grid, kThreads, 0, s>>>(p); break;
+    }
+    return cudaGetLastError();
+}
+
 template <typename T, int MODE>
 int var_grid_lc(int lc) {
     switch (lc) {
@@ -1553,6 +1775,24 @@ cudaError_t launch_var_pass(const VarParams& p, int dtype, int mode, int lc, int
                                  : var_launch_lc<__nv_bfloat16, kModeGrad>(p, lc, grid, s);
     return mode == kModeAdam ? var_launch_lc<__half, kModeAdam>(p, lc, grid, s)
                              : var_launch_lc<__half, kModeGrad>(p, lc, grid, s);
+}
+
+int grid_var_own(int dtype, int mode, int lc) {
+    if (dtype == kF32) return mode == kModeAdam ? own_grid_lc<float, kModeAdam>(lc) : own_grid_lc<float, kModeGrad>(lc);
+    if (dtype == kBF16)
+        return mode == kModeAdam ? own_grid_lc<__nv_bfloat16, kModeAdam>(lc) : own_grid_lc<__nv_bfloat16, kModeGrad>(lc);
+    return mode == kModeAdam ? own_grid_lc<__half, kModeAdam>(lc) : own_grid_lc<__half, kModeGrad>(lc);
+}
+
+cudaError_t launch_var_own(const VarParams& p, int dtype, int mode, int lc, int grid, cudaStream_t s) {
+    if (dtype == kF32)
+        return mode == kModeAdam ? own_launch_lc<float, kModeAdam>(p, lc, grid, s)
+                                 : own_launch_lc<float, kModeGrad>(p, lc, grid, s);
+    if (dtype == kBF16)
+        return mode == kModeAdam ? own_launch_lc<__nv_bfloat16, kModeAdam>(p, lc, grid, s)
+                                 : own_launch_lc<__nv_bfloat16, kModeGrad>(p, lc, grid, s);
+    return mode == kModeAdam ? own_launch_lc<__half, kModeAdam>(p, lc, grid, s)
+                             : own_launch_lc<__half, kModeGrad>(p, lc, grid, s);
 }
 
 int grid_var_ring(int dtype, int mode) {

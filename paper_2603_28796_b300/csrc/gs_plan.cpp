@@ -466,6 +466,63 @@ gs_status build_var(const int64_t* clause_ptr, const int32_t* lits, HostPlan& P)
     P.v_list.resize(P.vitems.size());
     std::vector<int32_t> fill(cnt.begin(), cnt.end() - 1);
     for (size_t k = 0; k < P.vitems.size(); ++k) P.v_list[fill[P.vitems[k].inst]++] = static_cast<int32_t>(k);
+
+    // Variable-owned items: consecutive whole variables of one instance, closed once they hold
+    // own_cap codes or kOwnVars variables (small formulas get smaller items, as with the tiles).
+    std::vector<int32_t> vk(n, -1);   // codes per occurrence of v if all equal, 0 mixed, -1 none
+    parallel_blocks(n, [&](int64_t v0, int64_t v1, int) {
+        for (int64_t v = v0; v < v1; ++v) {
+            int kk = -1;
+            for (int64_t q = code_start[v]; q < code_start[v + 1];) {
+                const int64_t q0 = q;
+                while (!(codes[q] & kVEnd)) ++q;
+                ++q;
+                kk = combine_kk(kk, static_cast<int>(q - q0));
+            }
+            vk[v] = kk;
+        }
+    });
+    const int64_t own_cap = std::max<int64_t>(256, std::min<int64_t>(kOwnCodes, code_start[n] / kMinTiles));
+    P.oitems.clear();
+    P.otab.clear();
+    for (int32_t inst = 0; inst < P.n_inst; ++inst) {
+        VarItem cur{};
+        int kk = -1;
+        bool open = false;
+        auto close_own = [&]() {
+            if (!open) return;
+            P.otab.push_back(static_cast<uint32_t>(cur.n_codes));
+            cur.kk = (kk >= 1 && kk <= 3) ? kk : 0;
+            P.oitems.push_back(cur);
+            open = false;
+        };
+        for (int64_t v = P.var_off[inst]; v < P.var_off[inst + 1]; ++v) {
+            if (!open) {
+                cur = VarItem{};
+                cur.code_base = code_start[v];
+                cur.vtab_base = static_cast<int64_t>(P.otab.size());
+                cur.v0 = static_cast<int32_t>(v);
+                cur.split = -1;
+                cur.inst = inst;
+                kk = -1;
+                open = true;
+            }
+            P.otab.push_back(static_cast<uint32_t>(code_start[v] - cur.code_base));
+            cur.nv++;
+            if (cost(v) > (int64_t(1) << 30)) P.own_ok = false;
+            cur.n_codes += static_cast<int32_t>(cost(v));
+            if (vk[v] != -1) kk = combine_kk(kk, vk[v]);
+            if (cur.n_codes >= own_cap || cur.nv >= kOwnVars) close_own();
+        }
+        close_own();
+    }
+    std::fill(cnt.begin(), cnt.end(), 0);
+    for (const VarItem& it : P.oitems) cnt[it.inst + 1]++;
+    for (int32_t i = 0; i < P.n_inst; ++i) cnt[i + 1] += cnt[i];
+    P.o_iptr = cnt;
+    P.o_list.resize(P.oitems.size());
+    std::vector<int32_t> ofill(cnt.begin(), cnt.end() - 1);
+    for (size_t k = 0; k < P.oitems.size(); ++k) P.o_list[ofill[P.oitems[k].inst]++] = static_cast<int32_t>(k);
     return GS_OK;
 }
 

@@ -25,8 +25,13 @@ struct HostPlan {
     std::vector<uint32_t> vtab;
     std::vector<VarItem> vitems;
     int32_t n_split = 0, n_split_rows = 0;
+    // variable-owned items: runs of whole variables (codes shared with the occurrence tiles);
+    // otab holds each item's nv + 1 code offsets relative to its first code
+    std::vector<uint32_t> otab;
+    std::vector<VarItem> oitems;
+    bool own_ok = true;   // false if a variable has too many codes for an item's 32-bit counts
     // per-instance tile lists (ascending tile ids)
-    std::vector<int32_t> f_iptr, f_list, v_iptr, v_list;
+    std::vector<int32_t> f_iptr, f_list, v_iptr, v_list, o_iptr, o_list;
 };
 
 // Validates a batch of formulas (instance-concatenated clause CSR, DIMACS literals local to

@@ -117,8 +117,42 @@ def test_fused_step(name, B, dtype, gather):
     """gather 1: register loads, 2: TMA gather4 ring where a chunk spans 32 lanes (B = 200)."""
     if gather == 2 and B != 200:
         pytest.skip("register loads are the only path below 32 lanes per chunk")
+    check_fused_step(name, B, dtype, var_gather=gather)
+
+
+@pytest.mark.parametrize("split", [1, 2])
+@pytest.mark.parametrize("lanes", [4, 8])
+@pytest.mark.parametrize("dtype", ["f32", "bf16", "f16"])
+@pytest.mark.parametrize("B", [5, 100])
+@pytest.mark.parametrize("name", ["3sat", "mixed", "edge", "community"])
+def test_fused_step_narrow_chunks(name, B, dtype, lanes, split):
+    """Chunks of 4 or 8 lanes (several lane groups per warp, several chunks at B = 100) with the
+    groups sharing each variable (split 1) or owning whole variables (split 2); the rounded bits
+    of chunks narrower than a 32-bit word go to the right word."""
+    check_fused_step(name, B, dtype, var_lanes=lanes, var_split=split)
+
+
+@pytest.mark.parametrize("dtype", ["f32", "bf16"])
+@pytest.mark.parametrize("name", ["3sat", "mixed", "community"])
+def test_backward_owned_variables(name, dtype):
+    """Gradient pass (gs_backward with per-candidate loss weights) with variable-owning groups."""
     cnf, prob = get(name)
-    _abi.gs_set_tuning(prob, var_gather=gather)
+    B = 40
+    _abi.gs_set_tuning(prob, var_lanes=8, var_split=2)
+    x = H.device_cands(synth.uniform_values(cnf.n_vars, B, seed=21), B, dtype)
+    xh = H.host64(x)
+    dl = torch.from_numpy(synth.normal_values(1, B, seed=22)[0].astype(np.float64)).cuda().reshape(1, B)
+    grad = _abi.gs_backward(prob, x, dloss=dl)
+    torch.cuda.synchronize()
+    g_ref, scale = oracle.backward(cnf.n_vars, cnf.clause_ptr, cnf.lits, xh)
+    w = dl.cpu().numpy()[0].astype(np.float32).astype(np.float64)
+    H.assert_grad(H.host64(grad), g_ref * w, scale * np.abs(w))
+    _abi.gs_set_tuning(prob)
+
+
+def check_fused_step(name, B, dtype, **tuning):
+    cnf, prob = get(name)
+    _abi.gs_set_tuning(prob, **tuning)
     n = cnf.n_vars
     t = 3
     d0 = synth.init_delta(n, B, seed=11)
@@ -320,7 +354,7 @@ def test_autotune_picks_a_valid_tuning_and_keeps_results():
     B = 200
     t = _abi.gs_autotune(prob, B, "f32")
     assert t["var_lanes"] in (4, 8, 16, 32) and t["fwd_lanes"] in (4, 8, 16, 32) and t["var_gather"] in (1, 2)
-    assert t["loss_mode"] in (1, 2)
+    assert t["loss_mode"] in (1, 2) and t["var_split"] in (1, 2)
     assert _abi.gs_get_tuning(prob) == t
     x = H.device_cands(synth.uniform_values(cnf.n_vars, B, seed=9), B)
     loss = _abi.gs_forward(prob, x)
