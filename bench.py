@@ -51,6 +51,10 @@ def parse():
     ap.add_argument("--leg-steps", type=int, default=50, help="timed steps of each extra leg")
     ap.add_argument("--var-lanes", type=int, default=0, help="cap on lanes per candidate chunk (gs_set_tuning)")
     ap.add_argument("--var-gather", type=int, default=0, help="0: automatic, 1: register loads, 2: TMA gather4 ring (gs_set_tuning)")
+    ap.add_argument("--var-split", type=int, default=0,
+                    help="0: automatic, 1: lane groups share each variable, 2: lane groups own whole variables (gs_set_tuning)")
+    ap.add_argument("--loss-mode", type=int, default=0,
+                    help="0: automatic, 1: loss credited in the variable pass, 2: separate forward pass (gs_set_tuning)")
     return ap.parse_args()
 
 
@@ -557,8 +561,9 @@ def run_native(args):
     if args.scale != 1.0:
         desc += " (formula scaled by %g: n=%d, m=%d)" % (args.scale, cnf.n_vars, cnf.n_clauses)
     prob = _abi.gs_load_cnf(cnf.n_vars, cnf.clause_ptr, cnf.lits)
-    if args.var_lanes or args.var_gather:
-        _abi.gs_set_tuning(prob, var_lanes=args.var_lanes, var_gather=args.var_gather)
+    if args.var_lanes or args.var_gather or args.var_split or args.loss_mode:
+        _abi.gs_set_tuning(prob, var_lanes=args.var_lanes, var_gather=args.var_gather, var_split=args.var_split,
+                           loss_mode=args.loss_mode)
     elif not args.no_autotune:
         _abi.gs_autotune(prob, B, dtype)
     tuning = _abi.gs_get_tuning(prob)

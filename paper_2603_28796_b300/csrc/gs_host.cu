@@ -93,7 +93,7 @@ struct gs_problem {
     int32_t* f_list = nullptr;
     int32_t* v_iptr = nullptr;
     int32_t* v_list = nullptr;
-    uint32_t* otab = nullptr;    // variable-owned items (lane groups own whole variables)
+    uint32_t* oent = nullptr;    // variable-owned items (lane groups own whole variables)
     VarItem* oitems = nullptr;
     int32_t* o_iptr = nullptr;
     int32_t* o_list = nullptr;
@@ -172,10 +172,11 @@ gs_status grow(T** ptr, size_t* cap, size_t need, cudaStream_t s, bool in_captur
 // The work-queue control words must be zero between launches (the kernels keep them so); a
 // fresh allocation is cleared once.
 gs_status grow_ctl(gs_problem* p, size_t need, cudaStream_t s, bool in_capture) {
-    const int32_t* before = p->ctl;
+    // a reallocation may return the old address, so compare capacities, not pointers
+    const size_t cap_before = p->ctl_cap;
     gs_status st = grow(&p->ctl, &p->ctl_cap, need, s, in_capture, "counters");
     if (st != GS_OK) return st;
-    if (p->ctl != before) GS_CUDA(cudaMemsetAsync(p->ctl, 0, sizeof(int32_t) * p->ctl_cap, s), "clear counters");
+    if (p->ctl_cap != cap_before) GS_CUDA(cudaMemsetAsync(p->ctl, 0, sizeof(int32_t) * p->ctl_cap, s), "clear counters");
     return GS_OK;
 }
 
@@ -280,7 +281,7 @@ gs_status load(int32_t n_inst, const int64_t* n_vars, const int64_t* n_clauses, 
         (st = upload(H.vrecs, &p->vrecs, &db, s)) != GS_OK || (st = upload(H.vtab, &p->vtab, &db, s)) != GS_OK ||
         (st = upload(H.vitems, &p->vitems, &db, s)) != GS_OK || (st = upload(H.f_iptr, &p->f_iptr, &db, s)) != GS_OK ||
         (st = upload(H.f_list, &p->f_list, &db, s)) != GS_OK || (st = upload(H.v_iptr, &p->v_iptr, &db, s)) != GS_OK ||
-        (st = upload(H.v_list, &p->v_list, &db, s)) != GS_OK || (st = upload(H.otab, &p->otab, &db, s)) != GS_OK ||
+        (st = upload(H.v_list, &p->v_list, &db, s)) != GS_OK || (st = upload(H.oent, &p->oent, &db, s)) != GS_OK ||
         (st = upload(H.oitems, &p->oitems, &db, s)) != GS_OK || (st = upload(H.o_iptr, &p->o_iptr, &db, s)) != GS_OK ||
         (st = upload(H.o_list, &p->o_list, &db, s)) != GS_OK ||
         (st = upload(H.inst_empty, &p->inst_empty, &db, s)) != GS_OK) {
@@ -305,7 +306,7 @@ gs_status load(int32_t n_inst, const int64_t* n_vars, const int64_t* n_clauses, 
     std::vector<uint16_t>().swap(H.vrecs);
     std::vector<uint32_t>().swap(H.vtab);
     std::vector<VarItem>().swap(H.vitems);
-    std::vector<uint32_t>().swap(H.otab);
+    std::vector<uint32_t>().swap(H.oent);
     std::vector<VarItem>().swap(H.oitems);
     *out = p;
     return GS_OK;
@@ -458,7 +459,7 @@ gs_status var_pass(gs_problem* p, int mode, const void* x_in, int dtype, int32_t
     if (own) {
         vp.items = p->oitems;
         vp.n_items = p->n_oitems;
-        vp.vtab = p->otab;
+        vp.vtab = p->oent;
     }
     const int64_t total = static_cast<int64_t>(vp.n_items) * c.n_chunks;
     if (total > 0) {
@@ -967,7 +968,7 @@ void gs_free(gs_problem* p) {
     int dev = -1;
     if (cudaGetDevice(&dev) == cudaSuccess && dev == p->device) cudaDeviceSynchronize();
     void* ptrs[] = {p->fcodes, p->fctab,  p->fitems, p->vcodes,     p->vrecs,  p->vtab,   p->vitems,
-                    p->f_iptr, p->f_list, p->v_iptr, p->v_list,     p->otab,   p->oitems, p->o_iptr,
+                    p->f_iptr, p->f_list, p->v_iptr, p->v_list,     p->oent,   p->oitems, p->o_iptr,
                     p->o_list, p->status, p->ctl,    p->inst_empty, p->part,   p->split,  p->bits,
                     p->part16, p->stage,  p->pool};
     for (void* q : ptrs)

@@ -256,7 +256,8 @@ cudaError_t launch_var_pass(const VarParams& p, int dtype, int mode, int lc, int
 // tmap: a CUtensorMap (128 bytes) over x_in as a 2-D tensor [n rows][B columns], box {32*VEC, 1}.
 cudaError_t launch_var_ring(const VarParams& p, const void* tmap, int dtype, int mode, int grid, cudaStream_t s);
 // Variable pass with variable-owning lane groups (lc = 4, 8 or 16 lanes per chunk): items and
-// vtab of p are the own-item table (whole variables, nv + 1 relative code offsets per item).
+// vtab of p are the own-item table (whole variables; vtab: one {row - v0, first code, end code,
+// 0} entry of 4 x uint32 per variable, in the order the lane groups take them).
 cudaError_t launch_var_own(const VarParams& p, int dtype, int mode, int lc, int grid, cudaStream_t s);
 int grid_var_own(int dtype, int mode, int lc);
 int grid_var_ring(int dtype, int mode);

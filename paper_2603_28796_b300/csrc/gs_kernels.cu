@@ -788,12 +788,13 @@ __global__ void __launch_bounds__(kThreads, Elem<T>::VEC == 4 ? 3 : 2) k_var_pas
 // ------------------------------------------------------------------------------------------
 // Variable-major pass with variable-owning lane groups (chunks of LC < 32 lanes). The same
 // arithmetic as k_var_pass, organised for small candidate rows: a work item is a run of whole
-// variables of about a few thousand codes, and each of the G = 32 / LC lane groups of the warp
-// takes a contiguous share of its variables (cut where the codes reach g / G of the item) and
-// runs each of them start to end: occurrence loop, gradient, epilogue. No group splits a
-// variable, so nothing is reduced across groups per variable and a group's batches of gathers
-// are only padded at the end of each of its variables. The codes are read straight from global
-// memory (each group reads its own contiguous run; consecutive batches share cache lines).
+// variables of about a few thousand codes, listed largest first, and each of the G = 32 / LC
+// lane groups of the warp takes every G-th of them and runs it start to end: occurrence loop,
+// gradient, epilogue. The groups thus work on variables of similar size side by side; no group
+// splits a variable, so nothing is reduced across groups per variable and a group's batches of
+// gathers are only padded at the end of each of its variables. The codes are read straight from
+// global memory (each group reads its variable's contiguous run; consecutive batches share
+// cache lines).
 template <typename T, int MODE, int LC>
 __device__ __forceinline__ void own_epilogue(const VarParams& P, int v, int inst, int chunk, int li, uint32_t gmask,
                                              const float (&ge)[Elem<T>::VEC], const AdamState<Elem<T>::VEC>& st) {
@@ -872,24 +873,9 @@ __device__ __forceinline__ void process_own_item(const VarParams& P, int w, int 
     const int item = w % P.n_items;
     const int chunk = w / P.n_items;
     const VarItem it = P.items[item];
-    const uint32_t* tab = P.vtab + it.vtab_base;   // nv + 1 code offsets, relative to code_base
+    // the item's variables in the order the groups take them: group g takes entries g, g + G, ...
+    const uint4* ent = reinterpret_cast<const uint4*>(P.vtab) + it.vtab_base;
     const uint32_t* cd = P.codes + it.code_base;
-    // group g owns variables [va, vb): the first variable whose codes start at or after
-    // n_codes * g / G opens its share; the last group takes everything to the end
-    auto share_start = [&](int gg) -> int {
-        if (gg >= G) return it.nv;
-        const uint32_t target = static_cast<uint32_t>((static_cast<int64_t>(it.n_codes) * gg) / G);
-        int lo = 0, hi = it.nv;
-        while (lo < hi) {
-            const int mid = (lo + hi) >> 1;
-            if (__ldg(tab + mid) < target)
-                lo = mid + 1;
-            else
-                hi = mid;
-        }
-        return lo;
-    };
-    const int va = share_start(g), vb = share_start(g + 1);
     const uint32_t gmask = (LC == 32) ? 0xffffffffu : (((1u << LC) - 1u) << (g * LC));
     const int lane_base = chunk * BC + li * VEC;
     const bool ld_ok = lane_base < P.B;
@@ -902,10 +888,10 @@ __device__ __forceinline__ void process_own_item(const VarParams& P, int w, int 
     float Ls[VEC], Lc[VEC];
 #pragma unroll
     for (int e = 0; e < VEC; ++e) Ls[e] = Lc[e] = 0.0f;
-    int cs = (va < vb) ? static_cast<int>(__ldg(tab + va)) : 0;
-    for (int vi = va; vi < vb; ++vi) {
-        const int ce = static_cast<int>(__ldg(tab + vi + 1));
-        const int v = it.v0 + vi;
+    for (int j = g; j < it.nv; j += G) {
+        const uint4 e = __ldg(ent + j);
+        const int v = it.v0 + static_cast<int>(e.x);
+        const int cs = static_cast<int>(e.y), ce = static_cast<int>(e.z);
         float gacc[VEC];
         Credits<H> cr;
 #pragma unroll
@@ -938,7 +924,6 @@ __device__ __forceinline__ void process_own_item(const VarParams& P, int w, int 
             }
         }
         own_epilogue<T, MODE, LC>(P, v, it.inst, chunk, li, gmask, gacc, st);
-        cs = ce;
     }
     __syncwarp();
     if (loss) {

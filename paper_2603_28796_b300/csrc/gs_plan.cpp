@@ -467,8 +467,11 @@ gs_status build_var(const int64_t* clause_ptr, const int32_t* lits, HostPlan& P)
     std::vector<int32_t> fill(cnt.begin(), cnt.end() - 1);
     for (size_t k = 0; k < P.vitems.size(); ++k) P.v_list[fill[P.vitems[k].inst]++] = static_cast<int32_t>(k);
 
-    // Variable-owned items: consecutive whole variables of one instance, closed once they hold
-    // own_cap codes or kOwnVars variables (small formulas get smaller items, as with the tiles).
+    // Variable-owned items: consecutive whole variables of one instance, closed at a multiple of
+    // 8 variables once they hold own_cap codes (or at kOwnVars variables, or the instance's end).
+    // Within an item the variables are listed in the order the lane groups take them: by code
+    // count, largest first (ties by row), so that the G groups, which take every G-th entry,
+    // work on variables of similar size at the same time.
     std::vector<int32_t> vk(n, -1);   // codes per occurrence of v if all equal, 0 mixed, -1 none
     parallel_blocks(n, [&](int64_t v0, int64_t v1, int) {
         for (int64_t v = v0; v < v1; ++v) {
@@ -484,14 +487,25 @@ gs_status build_var(const int64_t* clause_ptr, const int32_t* lits, HostPlan& P)
     });
     const int64_t own_cap = std::max<int64_t>(256, std::min<int64_t>(kOwnCodes, code_start[n] / kMinTiles));
     P.oitems.clear();
-    P.otab.clear();
+    P.oent.clear();
+    std::vector<int32_t> order;
     for (int32_t inst = 0; inst < P.n_inst; ++inst) {
         VarItem cur{};
         int kk = -1;
         bool open = false;
         auto close_own = [&]() {
             if (!open) return;
-            P.otab.push_back(static_cast<uint32_t>(cur.n_codes));
+            order.resize(cur.nv);
+            for (int32_t i = 0; i < cur.nv; ++i) order[i] = i;
+            std::stable_sort(order.begin(), order.end(),
+                             [&](int32_t a, int32_t b) { return cost(cur.v0 + a) > cost(cur.v0 + b); });
+            for (int32_t i : order) {
+                const int64_t v = cur.v0 + i;
+                P.oent.push_back(static_cast<uint32_t>(i));
+                P.oent.push_back(static_cast<uint32_t>(code_start[v] - cur.code_base));
+                P.oent.push_back(static_cast<uint32_t>(code_start[v + 1] - cur.code_base));
+                P.oent.push_back(0u);
+            }
             cur.kk = (kk >= 1 && kk <= 3) ? kk : 0;
             P.oitems.push_back(cur);
             open = false;
@@ -500,19 +514,18 @@ gs_status build_var(const int64_t* clause_ptr, const int32_t* lits, HostPlan& P)
             if (!open) {
                 cur = VarItem{};
                 cur.code_base = code_start[v];
-                cur.vtab_base = static_cast<int64_t>(P.otab.size());
+                cur.vtab_base = static_cast<int64_t>(P.oent.size() / 4);
                 cur.v0 = static_cast<int32_t>(v);
                 cur.split = -1;
                 cur.inst = inst;
                 kk = -1;
                 open = true;
             }
-            P.otab.push_back(static_cast<uint32_t>(code_start[v] - cur.code_base));
-            cur.nv++;
             if (cost(v) > (int64_t(1) << 30)) P.own_ok = false;
+            cur.nv++;
             cur.n_codes += static_cast<int32_t>(cost(v));
             if (vk[v] != -1) kk = combine_kk(kk, vk[v]);
-            if (cur.n_codes >= own_cap || cur.nv >= kOwnVars) close_own();
+            if ((cur.n_codes >= own_cap && cur.nv % 8 == 0) || cur.nv >= kOwnVars) close_own();
         }
         close_own();
     }
