@@ -297,6 +297,10 @@ __device__ __forceinline__ uint4 load_row(const RowView& rv, uint32_t u) {
     return ld_gather16(rv.base + static_cast<uint64_t>(u) * rv.row_bytes);
 }
 
+// Cache-line prefetches (no data returned; the lines are asked into L1 resp. L2).
+__device__ __forceinline__ void prefetch_l1(const void* p) { asm volatile("prefetch.global.L1 [%0];" ::"l"(p)); }
+__device__ __forceinline__ void prefetch_l2(const void* p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
+
 template <bool GC>
 __device__ __forceinline__ uint32_t ld_code(const uint32_t* cd, int i) {
     if constexpr (GC)
@@ -327,6 +331,9 @@ __device__ __forceinline__ void var_slots(const uint32_t* cd, int cs, int ce, co
     for (int s = cs; s < ce; s += NB) {
         uint32_t cw[NB];
         uint4 raw[NB];
+        if constexpr (GC) {
+            if (s + 32 < ce) prefetch_l1(cd + s + 32);   // the codes four batches ahead
+        }
 #pragma unroll
         for (int j = 0; j < NB; ++j) cw[j] = (s + j < ce) ? ld_code<GC>(cd, s + j) : (kVSentinel << kVShift);
 #pragma unroll
@@ -888,10 +895,22 @@ __device__ __forceinline__ void process_own_item(const VarParams& P, int w, int 
     float Ls[VEC], Lc[VEC];
 #pragma unroll
     for (int e = 0; e < VEC; ++e) Ls[e] = Lc[e] = 0.0f;
+    uint4 e = (g < it.nv) ? __ldg(ent + g) : make_uint4(0u, 0u, 0u, 0u);
     for (int j = g; j < it.nv; j += G) {
-        const uint4 e = __ldg(ent + j);
         const int v = it.v0 + static_cast<int>(e.x);
         const int cs = static_cast<int>(e.y), ce = static_cast<int>(e.z);
+        // ahead of use: the group's next variable's entry and first codes (L1), this variable's
+        // Adam state (L2; read after the gathers)
+        const uint4 en = (j + G < it.nv) ? __ldg(ent + j + G) : e;
+        if (j + G < it.nv) prefetch_l1(cd + en.y);
+        if constexpr (MODE == kModeAdam) {
+            if (ld_ok) {
+                const int64_t off = static_cast<int64_t>(v) * P.ldB + lane_base;
+                prefetch_l2(P.delta + off);
+                prefetch_l2(P.m + off);
+                prefetch_l2(P.v + off);
+            }
+        }
         float gacc[VEC];
         Credits<H> cr;
 #pragma unroll
@@ -924,6 +943,7 @@ __device__ __forceinline__ void process_own_item(const VarParams& P, int w, int 
             }
         }
         own_epilogue<T, MODE, LC>(P, v, it.inst, chunk, li, gmask, gacc, st);
+        e = en;
     }
     __syncwarp();
     if (loss) {
