@@ -110,6 +110,8 @@ struct gs_problem {
     size_t split_cap = 0;
     uint64_t* bits = nullptr;
     size_t bits_cap = 0;         // words
+    uint32_t* bits32c = nullptr; // low 32-bit word of each bit row (check of B <= 32)
+    size_t bits32c_cap = 0;
     uint16_t* part16 = nullptr;  // per-tile unsat counts
     size_t part16_cap = 0;
     unsigned char* pool = nullptr;   // candidate-pool selection workspace
@@ -140,11 +142,17 @@ bool capturing(cudaStream_t s) {
     return st != cudaStreamCaptureStatusNone;
 }
 
-// Stage-1 segments of the tile reductions: enough blocks to fill the GPU a few times over.
-int32_t n_segments(const gs_problem* p, int32_t B) {
-    const int64_t slices = static_cast<int64_t>((std::max(B, 1) + 31) / 32) * std::max(p->h.n_inst, 1);
-    const int64_t want = (4LL * p->sms + slices - 1) / slices;
-    return static_cast<int32_t>(std::min<int64_t>(32, std::max<int64_t>(1, want)));
+// Stage-1 segments of the tile reductions: each block (8 warps) sums one segment of an
+// instance's tiles, so about 64 tiles per segment keeps every warp's chain of dependent loads
+// short (at most 256 segments). max_tiles: the largest per-instance tile count of the list.
+constexpr int32_t kMaxSegments = 256;
+int32_t n_segments(int32_t max_tiles) {
+    return static_cast<int32_t>(std::min<int64_t>(kMaxSegments, std::max<int64_t>(1, (max_tiles + 63) / 64)));
+}
+int32_t max_list(const std::vector<int32_t>& iptr) {
+    int32_t mx = 0;
+    for (size_t i = 0; i + 1 < iptr.size(); ++i) mx = std::max(mx, iptr[i + 1] - iptr[i]);
+    return mx;
 }
 
 template <typename T>
@@ -198,12 +206,18 @@ gs_status ensure_ws(gs_problem* p, int dtype, int32_t B, bool need_bits, cudaStr
                        "bits")) != GS_OK)
             return st;
     }
+    if (B <= 32 && (st = grow(&p->bits32c, &p->bits32c_cap, std::max<size_t>(1, static_cast<size_t>(p->h.n)), s, cap,
+                               "compact bit rows")) != GS_OK)
+        return st;
     if ((st = grow(&p->part16, &p->part16_cap,
                    std::max<size_t>(1, static_cast<size_t>(p->n_fitems) * static_cast<size_t>(nwords(B)) * 64), s, cap,
                    "check partials")) != GS_OK)
         return st;
     if ((st = grow(&p->stage, &p->stage_cap,
-                   std::max<size_t>(1, static_cast<size_t>(n_segments(p, B)) * std::max(p->h.n_inst, 1) * std::max(B, 1)),
+                   std::max<size_t>(1, static_cast<size_t>(std::max({n_segments(max_list(p->h.f_iptr)),
+                                                                      n_segments(max_list(p->h.v_iptr)),
+                                                                      n_segments(max_list(p->h.o_iptr))})) *
+                                           std::max(p->h.n_inst, 1) * std::max(B, 1)),
                    s, cap, "reduction stage")) != GS_OK)
         return st;
     return GS_OK;
@@ -354,13 +368,20 @@ gs_status launch_check_all(gs_problem* p, const uint64_t* bits, int32_t B, int32
     cp.head = p->ctl + kCtlCheckHead;
     cp.exit_cnt = p->ctl + kCtlCheckExit;
     cp.status = p->status;
+    // at most 32 candidates: gather 32-bit words from a compact copy of the rows' low halves
+    const bool words32 = B <= 32 && p->bits32c != nullptr && p->bits32c_cap >= static_cast<size_t>(p->h.n);
     const int64_t total = static_cast<int64_t>(cp.n_items) * cp.n_wchunks;
     if (total > 0 && B > 0) {
-        const int grid = static_cast<int>(std::min<int64_t>(grid_check(lw), total));
-        GS_CUDA(launch_check(cp, lw, grid, s), "check kernel launch");
+        if (words32) {
+            GS_CUDA(launch_compact_low32(bits, p->h.n, nwd, p->bits32c, s), "bit-row compaction launch");
+            cp.bits = p->bits32c;
+        }
+        const int grid = static_cast<int>(std::min<int64_t>(grid_check(lw, words32), total));
+        GS_CUDA(launch_check(cp, lw, words32, grid, s), "check kernel launch");
     }
     GS_CUDA(launch_count_reduce(p->part16, nwd * 64, p->f_iptr, p->f_list, p->inst_empty, p->h.n_inst, B,
-                                n_segments(p, B), reinterpret_cast<int32_t*>(p->stage), unsat, best, s),
+                                n_segments(max_list(p->h.f_iptr)), reinterpret_cast<int32_t*>(p->stage), unsat, best,
+                                s),
             "count reduce launch");
     return GS_OK;
 }
@@ -477,7 +498,8 @@ gs_status var_pass(gs_problem* p, int mode, const void* x_in, int dtype, int32_t
     }
     if (loss)
         GS_CUDA(launch_loss_reduce2(p->part, c.bpad, own ? p->o_iptr : p->v_iptr, own ? p->o_list : p->v_list,
-                                    p->inst_empty, p->h.n_inst, B, n_segments(p, B), p->stage, loss, s),
+                                    p->inst_empty, p->h.n_inst, B,
+                                    n_segments(max_list(own ? p->h.o_iptr : p->h.v_iptr)), p->stage, loss, s),
                 "loss reduce launch");
     return GS_OK;
 }
@@ -522,6 +544,10 @@ gs_status gs_inspect_cnf(int64_t n_vars, int64_t n_clauses, const int64_t* claus
     bytes += (P.fcodes.size() * 4 + 64) + (P.fctab.size() * 2 + 64) + (P.fitems.size() * sizeof(FwdItem) + 64);
     bytes += (P.vcodes.size() * 4 + 64) + (P.vrecs.size() * 2 + 64) + (P.vtab.size() * 4 + 64) +
              (P.vitems.size() * sizeof(VarItem) + 64);
+    bytes += (P.oent.size() * 4 + 64) + (P.oitems.size() * sizeof(VarItem) + 64);
+    for (const std::vector<int32_t>* l : {&P.f_iptr, &P.f_list, &P.v_iptr, &P.v_list, &P.o_iptr, &P.o_list})
+        bytes += l->size() * 4 + 64;
+    bytes += (P.inst_empty.size() * 8 + 64) + (4 + 64);   // + the status word
     fill_info(P, static_cast<int64_t>(P.fitems.size()), static_cast<int64_t>(P.vitems.size()),
               static_cast<int64_t>(P.vcodes.size()), bytes, out);
     return GS_OK;
@@ -781,7 +807,7 @@ gs_status gs_reserve(gs_problem* p, int32_t B, gs_dtype dtype) {
     }
     tensor_map_encoder();
     grid_forward(dtype, cf.lc);
-    grid_check(lanes_for_words(nwords(B)));
+    grid_check(lanes_for_words(nwords(B)), B <= 32);
     if (dtype == GS_F32) {
         if ((st = ensure_st_ws(p, B, nullptr)) != GS_OK) return st;
         grid_st_pass(st_chunking(B).lw);
@@ -837,7 +863,7 @@ gs_status gs_forward(gs_problem* p, const void* x, gs_dtype dtype, int32_t B, in
         GS_CUDA(launch_forward(fp, dtype, c.lc, grid, s), "forward launch");
     }
     GS_CUDA(launch_loss_reduce2(p->part, c.bpad, p->f_iptr, p->f_list, p->inst_empty, p->h.n_inst, B,
-                                n_segments(p, B), p->stage, loss, s),
+                                n_segments(max_list(p->h.f_iptr)), p->stage, loss, s),
             "loss reduce launch");
     return GS_OK;
 }
@@ -970,7 +996,7 @@ void gs_free(gs_problem* p) {
     void* ptrs[] = {p->fcodes, p->fctab,  p->fitems, p->vcodes,     p->vrecs,  p->vtab,   p->vitems,
                     p->f_iptr, p->f_list, p->v_iptr, p->v_list,     p->oent,   p->oitems, p->o_iptr,
                     p->o_list, p->status, p->ctl,    p->inst_empty, p->part,   p->split,  p->bits,
-                    p->part16, p->stage,  p->pool};
+                    p->part16, p->stage,  p->pool,   p->bits32c};
     for (void* q : ptrs)
         if (q) cudaFree(q);
     delete p;

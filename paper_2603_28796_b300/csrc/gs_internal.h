@@ -230,7 +230,7 @@ struct CheckParams {
     int32_t nwd;             // uint64 words per row
     const uint32_t* codes;
     const uint16_t* ctab;
-    const uint64_t* bits;    // [n][nwd]
+    const void* bits;        // [n][nwd] uint64 words, or [n] uint32 words (low halves) when B <= 32
     uint16_t* part16;        // [n_items][bpad16] per-tile unsat counts
     int32_t bpad16;          // nwd * 64
     int32_t* head;
@@ -262,7 +262,10 @@ cudaError_t launch_var_own(const VarParams& p, int dtype, int mode, int lc, int 
 int grid_var_own(int dtype, int mode, int lc);
 int grid_var_ring(int dtype, int mode);
 cudaError_t launch_forward(const FwdParams& p, int dtype, int lc, int grid, cudaStream_t s);
-cudaError_t launch_check(const CheckParams& p, int lw, int grid, cudaStream_t s);
+// words32: p.bits holds one uint32 word per variable (B <= 32, lw == 1).
+cudaError_t launch_check(const CheckParams& p, int lw, bool words32, int grid, cudaStream_t s);
+// out[v] = low 32 bits of bits[v * nwd] for v < n (the candidates 0..31 of each row).
+cudaError_t launch_compact_low32(const uint64_t* bits, int64_t n, int32_t nwd, uint32_t* out, cudaStream_t s);
 cudaError_t launch_loss_reduce(const float* part, int32_t bpad, const int32_t* inst_items_ptr,
                                const int32_t* inst_items, const int64_t* n_empty, int32_t n_inst,
                                int32_t B, double* loss, cudaStream_t s);
@@ -291,6 +294,6 @@ cudaError_t launch_wait_selftest(int32_t* status, uint64_t limit_ns, cudaStream_
 // Occupancy-derived persistent grid size for a tiled kernel instantiation.
 int grid_var_pass(int dtype, int mode, int lc);
 int grid_forward(int dtype, int lc);
-int grid_check(int lw);
+int grid_check(int lw, bool words32 = false);
 
 }  // namespace gs

@@ -1342,9 +1342,11 @@ __global__ void __launch_bounds__(kThreads) k_forward(const FwdParams P) {
 // uint16 count per (tile, candidate). A fixed-order reduction over tiles follows; no atomics.
 constexpr int kPlanes = 9;
 
-template <int LW>
+template <int LW, typename W>
 __global__ void __launch_bounds__(kThreads) k_check(const CheckParams P) {
     constexpr int G = 32 / LW, NB = 8;
+    constexpr int WB = 8 * static_cast<int>(sizeof(W));   // candidates per word
+    const W* bitsw = static_cast<const W*>(P.bits);
     constexpr uint32_t kPad = 0xffffffffu;
     extern __shared__ __align__(128) unsigned char smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -1393,33 +1395,63 @@ __global__ void __launch_bounds__(kThreads) k_check(const CheckParams P) {
             const int cs = ct[(nc * g) / G];
             const int ce = ct[(nc * (g + 1)) / G];
             const bool ok_w = wd < P.nwd;
-            const int rem = P.B - wd * 64;
-            const uint64_t vmask = (!ok_w || rem <= 0) ? 0ull : (rem >= 64 ? ~0ull : ((1ull << rem) - 1ull));
-            uint64_t planes[kPlanes];
+            const int rem = P.B - wd * WB;
+            const W vmask = (!ok_w || rem <= 0) ? W(0) : (rem >= WB ? ~W(0) : static_cast<W>((W(1) << rem) - W(1)));
+            W planes[kPlanes];
 #pragma unroll
-            for (int p = 0; p < kPlanes; ++p) planes[p] = 0ull;
-            uint64_t acc = 0ull;
-            for (int s = cs; s < ce; s += NB) {
+            for (int p = 0; p < kPlanes; ++p) planes[p] = W(0);
+            W acc = W(0);
+            if constexpr (G >= 8) {
+                // narrow words (many lane groups): group g takes clauses g, g + G, ... so that the
+                // groups' code reads fall on different shared-memory banks
+                for (int c = g; c < nc; c += G) {
+                    const int a = ct[c], e = ct[c + 1];
+                    if (a == e) continue;   // empty clauses are counted per instance
+                    acc = W(0);
+                    for (int s = a; s < e; s += NB) {
+                        uint32_t cw[NB];
+                        W x[NB];
+#pragma unroll
+                        for (int j = 0; j < NB; ++j) cw[j] = (s + j < e) ? cd[s + j] : kPad;
+#pragma unroll
+                        for (int j = 0; j < NB; ++j)
+                            x[j] = (ok_w && cw[j] != kPad)
+                                       ? __ldg(bitsw + static_cast<int64_t>(cw[j] >> kFShift) * P.nwd + wd)
+                                       : W(0);
+#pragma unroll
+                        for (int j = 0; j < NB; ++j)
+                            if (cw[j] != kPad) acc |= (cw[j] & kFNeg) ? ~x[j] : x[j];
+                    }
+                    W carry = static_cast<W>(~acc & vmask);
+#pragma unroll
+                    for (int p = 0; p < kPlanes; ++p) {
+                        const W t = planes[p] & carry;
+                        planes[p] ^= carry;
+                        carry = t;
+                    }
+                }
+            }
+            for (int s = (G >= 8) ? ce : cs; s < ce; s += NB) {
                 uint32_t cw[NB];
-                uint64_t x[NB];
+                W x[NB];
 #pragma unroll
                 for (int j = 0; j < NB; ++j) cw[j] = (s + j < ce) ? cd[s + j] : kPad;
 #pragma unroll
                 for (int j = 0; j < NB; ++j)
                     x[j] = (ok_w && cw[j] != kPad)
-                               ? __ldg(P.bits + static_cast<int64_t>(cw[j] >> kFShift) * P.nwd + wd)
-                               : 0ull;
+                               ? __ldg(bitsw + static_cast<int64_t>(cw[j] >> kFShift) * P.nwd + wd)
+                               : W(0);
 #pragma unroll
                 for (int j = 0; j < NB; ++j) {
                     const uint32_t c = cw[j];
                     if (c == kPad) continue;
                     acc |= (c & kFNeg) ? ~x[j] : x[j];
                     if (c & kFEnd) {
-                        uint64_t carry = ~acc & vmask;
-                        acc = 0ull;
+                        W carry = static_cast<W>(~acc & vmask);
+                        acc = W(0);
 #pragma unroll
                         for (int p = 0; p < kPlanes; ++p) {
-                            const uint64_t t = planes[p] & carry;
+                            const W t = planes[p] & carry;
                             planes[p] ^= carry;
                             carry = t;
                         }
@@ -1428,28 +1460,28 @@ __global__ void __launch_bounds__(kThreads) k_check(const CheckParams P) {
             }
 #pragma unroll
             for (int off = LW; off < 32; off <<= 1) {
-                uint64_t carry = 0ull;
+                W carry = W(0);
 #pragma unroll
                 for (int p = 0; p < kPlanes; ++p) {
-                    const uint64_t a = planes[p];
-                    const uint64_t o = __shfl_xor_sync(0xffffffffu, a, off);
-                    const uint64_t sum = a ^ o ^ carry;
+                    const W a = planes[p];
+                    const W o = __shfl_xor_sync(0xffffffffu, a, off);
+                    const W sum = a ^ o ^ carry;
                     carry = (a & o) | (carry & (a ^ o));
                     planes[p] = sum;
                 }
             }
             if (ok_w) {
-                // every lane group now holds the word's totals: group g turns its 64 / G of the
-                // word's 64 counts into uint16 (pairs packed in uint32) and stores them
-                constexpr int PER = 64 / G;
+                // every lane group now holds the word's totals: group g turns its WB / G of the
+                // word's WB counts into uint16 (pairs packed in uint32) and stores them
+                constexpr int PER = WB / G;
                 const int c0 = g * PER;
-                uint16_t* dst16 = P.part16 + static_cast<int64_t>(item) * P.bpad16 + wd * 64 + c0;
+                uint16_t* dst16 = P.part16 + static_cast<int64_t>(item) * P.bpad16 + wd * WB + c0;
                 auto pair = [&](int b0) -> uint32_t {
                     uint32_t a = 0, b = 0;
 #pragma unroll
                     for (int p = 0; p < kPlanes; ++p) {
-                        a |= static_cast<uint32_t>((planes[p] >> b0) & 1ull) << p;
-                        b |= static_cast<uint32_t>((planes[p] >> (b0 + 1)) & 1ull) << p;
+                        a |= static_cast<uint32_t>((planes[p] >> b0) & W(1)) << p;
+                        b |= static_cast<uint32_t>((planes[p] >> (b0 + 1)) & W(1)) << p;
                     }
                     return a | (b << 16);
                 };
@@ -1459,10 +1491,15 @@ __global__ void __launch_bounds__(kThreads) k_check(const CheckParams P) {
                     for (int q = 0; q < PER / 8; ++q)
                         dst[q] = make_uint4(pair(c0 + 8 * q), pair(c0 + 8 * q + 2), pair(c0 + 8 * q + 4),
                                             pair(c0 + 8 * q + 6));
-                } else {
+                } else if constexpr (PER >= 2) {
                     uint32_t* dst = reinterpret_cast<uint32_t*>(dst16);
 #pragma unroll
                     for (int q = 0; q < PER / 2; ++q) dst[q] = pair(c0 + 2 * q);
+                } else {
+                    uint32_t a = 0;
+#pragma unroll
+                    for (int p = 0; p < kPlanes; ++p) a |= static_cast<uint32_t>((planes[p] >> c0) & W(1)) << p;
+                    *dst16 = static_cast<uint16_t>(a);
                 }
             }
         }
@@ -1471,6 +1508,14 @@ __global__ void __launch_bounds__(kThreads) k_check(const CheckParams P) {
         buf ^= 1;
     }
     queue_exit(P.head, P.exit_cnt);
+}
+
+// Low 32-bit word of each row of a bit-packed assignment (the candidates 0..31), for the check
+// of batches of at most 32 candidates: half the bytes a check gathers per literal.
+__global__ void __launch_bounds__(256) k_compact_low32(const uint64_t* bits, int64_t n, int32_t nwd, uint32_t* out) {
+    for (int64_t v = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; v < n;
+         v += static_cast<int64_t>(gridDim.x) * blockDim.x)
+        out[v] = static_cast<uint32_t>(__ldcs(bits + v * nwd));
 }
 
 // ------------------------------------------------------------------------------------------
@@ -1490,8 +1535,10 @@ __global__ void __launch_bounds__(256) k_reduce_tiles(const PT* part, int32_t st
     const int k0 = a + seg * per;
     const int k1 = min(e, k0 + per);
     AT s = AT(0);
-    if (b < B)
+    if (b < B) {
+#pragma unroll 4
         for (int k = k0 + warp; k < k1; k += 8) s += static_cast<AT>(part[static_cast<int64_t>(items[k]) * stride + b]);
+    }
     red[warp][lane] = s;
     __syncthreads();
     if (warp == 0 && b < B) {
@@ -1508,6 +1555,7 @@ __global__ void __launch_bounds__(256) k_loss_final(const double* stage, int32_t
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= B) return;
     double t = 0.0;
+#pragma unroll 8
     for (int sgm = 0; sgm < n_seg; ++sgm) t += stage[(static_cast<int64_t>(sgm) * n_inst + inst) * B + b];
     loss[static_cast<int64_t>(inst) * B + b] = t + static_cast<double>(n_empty[inst]);
 }
@@ -1523,6 +1571,7 @@ __global__ void __launch_bounds__(1024) k_count_final(const int32_t* stage, int3
     unsigned long long key = ~0ull;
     for (int b = threadIdx.x; b < B; b += blockDim.x) {
         int32_t c = add;
+#pragma unroll 8
         for (int sgm = 0; sgm < n_seg; ++sgm) c += stage[(static_cast<int64_t>(sgm) * n_inst + inst) * B + b];
         unsat[static_cast<int64_t>(inst) * B + b] = c;
         const unsigned long long k = (static_cast<unsigned long long>(static_cast<uint32_t>(c)) << 32) |
@@ -1661,10 +1710,10 @@ int fwd_grid_t() {
     if (!grid) grid = persistent_grid(k_forward<T, LC>, kWarps * kFwdWarpBytes);
     return grid;
 }
-template <int LW>
+template <int LW, typename W>
 int check_grid_t() {
     static int grid = 0;
-    if (!grid) grid = persistent_grid(k_check<LW>, kWarps * kFwdWarpBytes);
+    if (!grid) grid = persistent_grid(k_check<LW, W>, kWarps * kFwdWarpBytes);
     return grid;
 }
 
@@ -1760,14 +1809,15 @@ int grid_forward(int dtype, int lc) {
     if (dtype == kBF16) return fwd_grid_lc<__nv_bfloat16>(lc);
     return fwd_grid_lc<__half>(lc);
 }
-int grid_check(int lw) {
+int grid_check(int lw, bool words32) {
+    if (words32) return check_grid_t<1, uint32_t>();
     switch (lw) {
-        case 32: return check_grid_t<32>();
-        case 16: return check_grid_t<16>();
-        case 8: return check_grid_t<8>();
-        case 4: return check_grid_t<4>();
-        case 2: return check_grid_t<2>();
-        default: return check_grid_t<1>();
+        case 32: return check_grid_t<32, uint64_t>();
+        case 16: return check_grid_t<16, uint64_t>();
+        case 8: return check_grid_t<8, uint64_t>();
+        case 4: return check_grid_t<4, uint64_t>();
+        case 2: return check_grid_t<2, uint64_t>();
+        default: return check_grid_t<1, uint64_t>();
     }
 }
 
@@ -1836,16 +1886,27 @@ cudaError_t launch_forward(const FwdParams& p, int dtype, int lc, int grid, cuda
     return fwd_launch_lc<__half>(p, lc, grid, s);
 }
 
-cudaError_t launch_check(const CheckParams& p, int lw, int grid, cudaStream_t s) {
+cudaError_t launch_check(const CheckParams& p, int lw, bool words32, int grid, cudaStream_t s) {
     const int smem = kWarps * kFwdWarpBytes;
-    switch (lw) {
-        case 32: check_grid_t<32>(); k_check<32><<<grid, kThreads, smem, s>>>(p); break;
-        case 16: check_grid_t<16>(); k_check<16><<<grid, kThreads, smem, s>>>(p); break;
-        case 8: check_grid_t<8>(); k_check<8><<<grid, kThreads, smem, s>>>(p); break;
-        case 4: check_grid_t<4>(); k_check<4><<<grid, kThreads, smem, s>>>(p); break;
-        case 2: check_grid_t<2>(); k_check<2><<<grid, kThreads, smem, s>>>(p); break;
-        default: check_grid_t<1>(); k_check<1><<<grid, kThreads, smem, s>>>(p); break;
+    if (words32) {
+        check_grid_t<1, uint32_t>();
+        k_check<1, uint32_t><<<grid, kThreads, smem, s>>>(p);
+        return cudaGetLastError();
     }
+    switch (lw) {
+        case 32: check_grid_t<32, uint64_t>(); k_check<32, uint64_t><<<grid, kThreads, smem, s>>>(p); break;
+        case 16: check_grid_t<16, uint64_t>(); k_check<16, uint64_t><<<grid, kThreads, smem, s>>>(p); break;
+        case 8: check_grid_t<8, uint64_t>(); k_check<8, uint64_t><<<grid, kThreads, smem, s>>>(p); break;
+        case 4: check_grid_t<4, uint64_t>(); k_check<4, uint64_t><<<grid, kThreads, smem, s>>>(p); break;
+        case 2: check_grid_t<2, uint64_t>(); k_check<2, uint64_t><<<grid, kThreads, smem, s>>>(p); break;
+        default: check_grid_t<1, uint64_t>(); k_check<1, uint64_t><<<grid, kThreads, smem, s>>>(p); break;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_compact_low32(const uint64_t* bits, int64_t n, int32_t nwd, uint32_t* out, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    k_compact_low32<<<elementwise_grid(n), 256, 0, s>>>(bits, n, nwd, out);
     return cudaGetLastError();
 }
 

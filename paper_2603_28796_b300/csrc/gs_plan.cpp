@@ -191,9 +191,48 @@ int tile_cap(int64_t count, int cap) {
 
 // Clause tiles: consecutive whole clauses of one instance, <= kFwdCodes codes, <= kFwdClauses.
 // One code per literal in literal order, so a tile's codes start at its first clause's offset.
+// Clause tiles: whole clauses of one instance, <= kFwdCodes codes, <= kFwdClauses. The tiles
+// take the clauses in the order of their median literal's variable row (a stable counting sort;
+// an empty clause keys on its instance's first row), so that a tile's literals fall on nearby
+// rows when the formula has locality (clauses of one community, chains of one long clause)
+// and the rows a tile gathers stay in cache. The loss and the counts are sums over all clauses,
+// so the order changes only the float32 summation order of the loss. Codes are stored in tile
+// order, one per literal in literal order within each clause.
 void build_fwd(const int64_t* clause_ptr, const int32_t* lits, HostPlan& P) {
     const int clause_cap = tile_cap(P.m, kFwdClauses);
-    std::vector<int64_t> first;   // first clause of each tile
+    const int64_t m = P.m, n = P.n;
+    // sort key of every clause: its median literal's variable row
+    std::vector<int64_t> key(m);
+    parallel_blocks(m, [&](int64_t t0, int64_t t1, int) {
+        int32_t inst = t0 < m ? inst_of_clause(P, t0) : 0;
+        std::vector<int64_t> rows;
+        for (int64_t t = t0; t < t1; ++t) {
+            while (t >= P.clause_off[inst + 1]) ++inst;
+            const int64_t a = clause_ptr[t], b = clause_ptr[t + 1];
+            if (a == b) {
+                key[t] = P.var_off[inst];
+                continue;
+            }
+            rows.clear();
+            for (int64_t j = a; j < b; ++j) rows.push_back(lit_row(P, inst, lits[j]));
+            std::nth_element(rows.begin(), rows.begin() + (b - a) / 2, rows.end());
+            key[t] = rows[(b - a) / 2];
+        }
+    });
+    // stable counting sort by key: instances stay contiguous and in order, since instance i's
+    // rows (and the first-row key of its empty clauses) precede instance i + 1's
+    std::vector<int64_t> order(m);
+    {
+        std::vector<int64_t> cnt(n + 2, 0);
+        for (int64_t t = 0; t < m; ++t) cnt[key[t] + 1]++;
+        for (int64_t r = 0; r <= n; ++r) cnt[r + 1] += cnt[r];
+        for (int64_t t = 0; t < m; ++t) order[cnt[key[t]]++] = t;
+    }
+    std::vector<int64_t>().swap(key);
+    // tiles over the sorted sequence; code offsets of the sorted clauses
+    std::vector<int64_t> pos_code(m + 1, 0);
+    for (int64_t i = 0; i < m; ++i) pos_code[i + 1] = pos_code[i] + (clause_ptr[order[i] + 1] - clause_ptr[order[i]]);
+    std::vector<int64_t> first;   // first sorted position of each tile
     P.f_iptr.assign(P.n_inst + 1, 0);
     int64_t ctab = 0;
     for (int32_t inst = 0; inst < P.n_inst; ++inst) {
@@ -201,13 +240,13 @@ void build_fwd(const int64_t* clause_ptr, const int32_t* lits, HostPlan& P) {
         const int64_t te = P.clause_off[inst + 1];
         while (t < te) {
             FwdItem it{};
-            it.code_base = clause_ptr[t];
+            it.code_base = pos_code[t];
             it.ctab_base = ctab;
             it.inst = inst;
             first.push_back(t);
             int nc = 0, ncodes = 0;
             while (t < te && nc < clause_cap) {
-                const int k = static_cast<int>(clause_ptr[t + 1] - clause_ptr[t]);
+                const int k = static_cast<int>(pos_code[t + 1] - pos_code[t]);
                 if (ncodes + k > kFwdCodes) break;
                 ncodes += k;
                 ++nc;
@@ -227,9 +266,10 @@ void build_fwd(const int64_t* clause_ptr, const int32_t* lits, HostPlan& P) {
             const FwdItem& it = P.fitems[i];
             const int64_t t0 = first[i];
             uint16_t* tab = &P.fctab[it.ctab_base];
+            uint32_t* dst = &P.fcodes[it.code_base];
             int ncodes = 0;
             for (int c = 0; c < it.n_clauses; ++c) {
-                const int64_t t = t0 + c;
+                const int64_t t = order[t0 + c];
                 const int64_t a = clause_ptr[t], b = clause_ptr[t + 1];
                 tab[c] = static_cast<uint16_t>(ncodes);
                 for (int64_t j = a; j < b; ++j) {
@@ -237,9 +277,8 @@ void build_fwd(const int64_t* clause_ptr, const int32_t* lits, HostPlan& P) {
                     uint32_t code = static_cast<uint32_t>(lit_row(P, it.inst, l)) << kFShift;
                     if (l < 0) code |= kFNeg;
                     if (j == b - 1) code |= kFEnd;
-                    P.fcodes[j] = code;
+                    dst[ncodes++] = code;
                 }
-                ncodes += static_cast<int>(b - a);
             }
             tab[it.n_clauses] = static_cast<uint16_t>(ncodes);
         }

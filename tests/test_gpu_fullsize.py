@@ -59,6 +59,45 @@ def test_differentiation_fused_step_sampled_parity():
     assert np.array_equal(H.unpack_bits(bits, n, B), (dg > 0).astype(np.uint8))   # all columns
 
 
+def test_structured_owned_variables_step_and_check_sampled():
+    """Community-structured workload at full size (n = 10,000,000, m = 42,000,000, B = 32, BF16)
+    in the benchmark's configuration: variable-owning lane groups with the loss credited in the
+    pass, then the exact check of the rounded bits (32-bit word path). Sampled columns against
+    the oracle; the bits of every column against [delta' > 0]."""
+    cnf, prob = workload("structured")
+    n, B, t = cnf.n_vars, 32, 2
+    _abi.gs_set_tuning(prob, var_split=2, loss_mode=1)
+    S = np.array([0, 1, 17, 31])
+    d0 = synth.init_delta(n, B, seed=111)
+    m0 = synth.normal_values(n, B, seed=112, scale=0.02)
+    v0 = np.abs(synth.normal_values(n, B, seed=113, scale=0.005))
+    xin = H.device_cands(synth.uniform_values(n, B, seed=114), B, "bf16")
+    delta, m, v = (H.device_cands(a, B) for a in (d0, m0, v0))
+    xout = candidates(n, B, torch.bfloat16)
+    loss = torch.zeros((1, B), dtype=torch.float64, device="cuda")
+    bits = torch.zeros((n, 1), dtype=torch.int64, device="cuda")
+    _abi.gs_step(prob, delta, m, v, t, x_in=xin, x_out=xout, loss=loss, bits=bits)
+    unsat, best = _abi.gs_check_bits(prob, bits, B)
+    torch.cuda.synchronize()
+    _abi.gs_sync_status(prob)
+    xh = H.host64(xin)[:, S]
+    lu, _ = oracle.forward(n, cnf.clause_ptr, cnf.lits, xh)
+    H.assert_loss(loss.cpu().numpy()[0][S], lu, "structured loss")
+    g_ref, scale = oracle.backward(n, cnf.clause_ptr, cnf.lits, xh)
+    d_ref, m_ref, v_ref, _ = oracle.adam(d0[:, S], m0[:, S], v0[:, S], g_ref, t)
+    tol = H.adam_tolerances(d0[:, S], m0[:, S], v0[:, S], g_ref, scale, t)
+    dg = H.host64(delta)
+    out = dict(delta=dg[:, S], m=H.host64(m)[:, S], v=H.host64(v)[:, S])
+    H.check_adam(out, dict(delta=d_ref, m=m_ref, v=v_ref), tol, "structured workload")
+    assert np.array_equal(H.unpack_bits(bits, n, B), (dg > 0).astype(np.uint8))
+    _, u_ref, _ = oracle.round_check(n, cnf.clause_ptr, cnf.lits, dg[:, S])
+    u = unsat.cpu().numpy()[0]
+    assert np.array_equal(u[S], u_ref)
+    b = int(best.cpu()[0])
+    assert u[b] == u.min() and np.all(u[:b] > u.min())
+    _abi.gs_set_tuning(prob)
+
+
 def test_differentiation_round_check_sampled():
     cnf, prob = workload("differentiation")
     n, B = cnf.n_vars, 1024

@@ -203,7 +203,7 @@ def test_step_with_external_gradient(dtype):
     H.check_adam(dict(delta=H.host64(delta), m=H.host64(m), v=H.host64(v)), dict(delta=d_ref, m=m_ref, v=v_ref), tol)
 
 
-@pytest.mark.parametrize("B", [1, 63, 64, 65, 130, 1000])
+@pytest.mark.parametrize("B", [1, 17, 32, 33, 63, 64, 65, 130, 1000])
 @pytest.mark.parametrize("name", ["3sat", "mixed", "edge", "community"])
 def test_round_check_bit_exact(name, B):
     cnf, prob = get(name)
