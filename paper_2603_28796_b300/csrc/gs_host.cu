@@ -142,12 +142,16 @@ bool capturing(cudaStream_t s) {
     return st != cudaStreamCaptureStatusNone;
 }
 
-// Stage-1 segments of the tile reductions: each block (8 warps) sums one segment of an
-// instance's tiles, so about 64 tiles per segment keeps every warp's chain of dependent loads
-// short (at most 256 segments). max_tiles: the largest per-instance tile count of the list.
+// Stage-1 segments of the tile reductions: enough blocks (segments x 32-candidate slices x
+// instances) to fill the GPU a few times over, but no segment shorter than 32 tiles, and at
+// most 256 (a formula of 400,000 tiles and one slice gets 256 segments of ~1,600 tiles; 2,000
+// tiles and 32 slices get 19). max_tiles: the largest per-instance tile count of the list.
 constexpr int32_t kMaxSegments = 256;
-int32_t n_segments(int32_t max_tiles) {
-    return static_cast<int32_t>(std::min<int64_t>(kMaxSegments, std::max<int64_t>(1, (max_tiles + 63) / 64)));
+int32_t n_segments(const gs_problem* p, int32_t B, int32_t max_tiles) {
+    const int64_t slices = static_cast<int64_t>((std::max(B, 1) + 31) / 32) * std::max(p->h.n_inst, 1);
+    const int64_t fill = (4LL * p->sms + slices - 1) / slices;
+    const int64_t want = std::min<int64_t>(fill, (static_cast<int64_t>(max_tiles) + 31) / 32);
+    return static_cast<int32_t>(std::min<int64_t>(kMaxSegments, std::max<int64_t>(1, want)));
 }
 int32_t max_list(const std::vector<int32_t>& iptr) {
     int32_t mx = 0;
@@ -214,9 +218,9 @@ gs_status ensure_ws(gs_problem* p, int dtype, int32_t B, bool need_bits, cudaStr
                    "check partials")) != GS_OK)
         return st;
     if ((st = grow(&p->stage, &p->stage_cap,
-                   std::max<size_t>(1, static_cast<size_t>(std::max({n_segments(max_list(p->h.f_iptr)),
-                                                                      n_segments(max_list(p->h.v_iptr)),
-                                                                      n_segments(max_list(p->h.o_iptr))})) *
+                   std::max<size_t>(1, static_cast<size_t>(std::max({n_segments(p, B, max_list(p->h.f_iptr)),
+                                                                      n_segments(p, B, max_list(p->h.v_iptr)),
+                                                                      n_segments(p, B, max_list(p->h.o_iptr))})) *
                                            std::max(p->h.n_inst, 1) * std::max(B, 1)),
                    s, cap, "reduction stage")) != GS_OK)
         return st;
@@ -380,7 +384,7 @@ gs_status launch_check_all(gs_problem* p, const uint64_t* bits, int32_t B, int32
         GS_CUDA(launch_check(cp, lw, words32, grid, s), "check kernel launch");
     }
     GS_CUDA(launch_count_reduce(p->part16, nwd * 64, p->f_iptr, p->f_list, p->inst_empty, p->h.n_inst, B,
-                                n_segments(max_list(p->h.f_iptr)), reinterpret_cast<int32_t*>(p->stage), unsat, best,
+                                n_segments(p, B, max_list(p->h.f_iptr)), reinterpret_cast<int32_t*>(p->stage), unsat, best,
                                 s),
             "count reduce launch");
     return GS_OK;
@@ -499,7 +503,7 @@ gs_status var_pass(gs_problem* p, int mode, const void* x_in, int dtype, int32_t
     if (loss)
         GS_CUDA(launch_loss_reduce2(p->part, c.bpad, own ? p->o_iptr : p->v_iptr, own ? p->o_list : p->v_list,
                                     p->inst_empty, p->h.n_inst, B,
-                                    n_segments(max_list(own ? p->h.o_iptr : p->h.v_iptr)), p->stage, loss, s),
+                                    n_segments(p, B, max_list(own ? p->h.o_iptr : p->h.v_iptr)), p->stage, loss, s),
                 "loss reduce launch");
     return GS_OK;
 }
@@ -863,7 +867,7 @@ gs_status gs_forward(gs_problem* p, const void* x, gs_dtype dtype, int32_t B, in
         GS_CUDA(launch_forward(fp, dtype, c.lc, grid, s), "forward launch");
     }
     GS_CUDA(launch_loss_reduce2(p->part, c.bpad, p->f_iptr, p->f_list, p->inst_empty, p->h.n_inst, B,
-                                n_segments(max_list(p->h.f_iptr)), p->stage, loss, s),
+                                n_segments(p, B, max_list(p->h.f_iptr)), p->stage, loss, s),
             "loss reduce launch");
     return GS_OK;
 }

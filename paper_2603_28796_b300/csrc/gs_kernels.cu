@@ -1552,15 +1552,27 @@ __global__ void __launch_bounds__(256) k_reduce_tiles(const PT* part, int32_t st
     }
 }
 
+// Stage 2 of the loss: block (32-candidate slice, instance); its 8 warps sum the segments
+// round-robin, then combine in warp order; empty clauses (product 1 each) are added.
 __global__ void __launch_bounds__(256) k_loss_final(const double* stage, int32_t n_seg, int32_t n_inst,
                                                     const int64_t* n_empty, int32_t B, double* loss) {
+    __shared__ double red[8][32];
     const int inst = blockIdx.y;
-    const int b = blockIdx.x * blockDim.x + threadIdx.x;
-    if (b >= B) return;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int b = blockIdx.x * 32 + lane;
     double t = 0.0;
-#pragma unroll 8
-    for (int sgm = 0; sgm < n_seg; ++sgm) t += stage[(static_cast<int64_t>(sgm) * n_inst + inst) * B + b];
-    loss[static_cast<int64_t>(inst) * B + b] = t + static_cast<double>(n_empty[inst]);
+    if (b < B) {
+#pragma unroll 4
+        for (int sgm = warp; sgm < n_seg; sgm += 8) t += stage[(static_cast<int64_t>(sgm) * n_inst + inst) * B + b];
+    }
+    red[warp][lane] = t;
+    __syncthreads();
+    if (warp == 0 && b < B) {
+        double u = 0.0;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) u += red[q][lane];
+        loss[static_cast<int64_t>(inst) * B + b] = u + static_cast<double>(n_empty[inst]);
+    }
 }
 
 // Per instance: unsat = sum of the segments + empty clauses (always unsatisfied); best = the
@@ -1928,7 +1940,7 @@ cudaError_t launch_loss_reduce2(const float* part, int32_t bpad, const int32_t* 
     if (B <= 0 || n_inst <= 0) return cudaSuccess;
     k_reduce_tiles<float, double><<<dim3((B + 31) / 32, n_inst, n_seg), 256, 0, s>>>(part, bpad, iptr, items, B,
                                                                                       n_seg, stage);
-    k_loss_final<<<dim3((B + 255) / 256, n_inst), 256, 0, s>>>(stage, n_seg, n_inst, n_empty, B, loss);
+    k_loss_final<<<dim3((B + 31) / 32, n_inst), 256, 0, s>>>(stage, n_seg, n_inst, n_empty, B, loss);
     return cudaGetLastError();
 }
 
