@@ -278,6 +278,45 @@ def test_batch_instances():
         off += p.n_vars
 
 
+@pytest.mark.parametrize("split", [1, 2])
+@pytest.mark.parametrize("dtype", ["f32", "bf16"])
+def test_batch_instances_fused_step(dtype, split):
+    """Fused step on a batch of instances (per-instance credited losses), with lane groups sharing
+    each variable (split 1) or owning whole variables (split 2): owned-variable items never span
+    two instances and their loss partials are reduced per instance."""
+    parts = [synth.planted_ksat(300 + 50 * i, int(4.2 * (300 + 50 * i)), 3 + (i % 2), seed=70 + i) for i in range(4)]
+    parts.append(edge_cnf())
+    parts.append(synth.mixed_powerlaw(600, 2000, seed=75))
+    batch = synth.concat(parts)
+    prob = _abi.gs_load_batch(batch.n_vars, batch.n_clauses, batch.clause_ptr, batch.lits)
+    _abi.gs_set_tuning(prob, var_lanes=8, var_split=split, loss_mode=1)
+    n, B, t = int(batch.n_vars.sum()), 40, 2
+    d0 = synth.init_delta(n, B, seed=71)
+    m0 = synth.normal_values(n, B, seed=72, scale=0.05)
+    v0 = np.abs(synth.normal_values(n, B, seed=73, scale=0.01))
+    xin = H.device_cands(synth.uniform_values(n, B, seed=74), B, dtype)
+    delta, m, v = (H.device_cands(a, B) for a in (d0, m0, v0))
+    xout = candidates(n, B, H.TORCH_DT[dtype])
+    loss = torch.zeros((len(parts), B), dtype=torch.float64, device="cuda")
+    bits = torch.zeros((n, 1), dtype=torch.int64, device="cuda")
+    _abi.gs_step(prob, delta, m, v, t, x_in=xin, x_out=xout, loss=loss, bits=bits)
+    torch.cuda.synchronize()
+    xh, dg = H.host64(xin), H.host64(delta)
+    off = 0
+    for i, p in enumerate(parts):
+        rows = slice(off, off + p.n_vars)
+        lu, _ = oracle.forward(p.n_vars, p.clause_ptr, p.lits, xh[rows])
+        H.assert_loss(loss.cpu().numpy()[i], lu, "instance %d loss" % i)
+        g_ref, scale = oracle.backward(p.n_vars, p.clause_ptr, p.lits, xh[rows])
+        d_ref, m_ref, v_ref, _ = oracle.adam(d0[rows, :B], m0[rows, :B], v0[rows, :B], g_ref, t)
+        tol = H.adam_tolerances(d0[rows, :B], m0[rows, :B], v0[rows, :B], g_ref, scale, t)
+        out = dict(delta=dg[rows], m=H.host64(m)[rows], v=H.host64(v)[rows])
+        H.check_adam(out, dict(delta=d_ref, m=m_ref, v=v_ref), tol, "instance %d" % i)
+        off += p.n_vars
+    assert np.array_equal(H.unpack_bits(bits, n, B), (dg > 0).astype(np.uint8))
+    prob.close()
+
+
 def test_deterministic_bitwise():
     cnf, prob = get("mixed")
     B = 128
