@@ -1363,12 +1363,25 @@ __global__ void __launch_bounds__(kThreads) k_check(const CheckParams P) {
     }
     __syncwarp();
     const int total = P.n_items * P.n_wchunks;
-    int w = fetch_work(P.head, lane);
+    // 32-bit words (B <= 32): each warp takes a fixed contiguous range of tiles instead of
+    // pulling from the queue, so a CTA's warps work on neighbouring tiles (with tiles sorted by
+    // median row, the same rows); the kernel runs 2 CTAs per SM and leaves the rest of the
+    // SM's memory to L1, where those rows' compact words stay (community formula: 1.78 ->
+    // 0.84 ms per check)
+    constexpr bool STATIC = sizeof(W) == 4;
+    const int gw = blockIdx.x * kWarps + warp, nw = gridDim.x * kWarps;
+    const int per = (total + nw - 1) / nw;
+    const int w_end = min(total, (gw + 1) * per);
+    auto next_w = [&](int cur) -> int {
+        if constexpr (STATIC) return (cur + 1 < w_end) ? cur + 1 : total;
+        else return fetch_work(P.head, lane);
+    };
+    int w = STATIC ? ((gw * per < total) ? gw * per : total) : fetch_work(P.head, lane);
     if (w < total && lane == 0) issue_fwd_item(P.items, P.codes, P.ctab, w % P.n_items, wbase, &bars[0]);
     uint32_t phase[2] = {0u, 0u};
     int buf = 0;
     while (w < total) {
-        const int wn = fetch_work(P.head, lane);
+        const int wn = next_w(w);
         if (wn < total && lane == 0) {
             fence_proxy_async();
             issue_fwd_item(P.items, P.codes, P.ctab, wn % P.n_items, wbase + (buf ^ 1) * kFwdBufBytes, &bars[buf ^ 1]);
@@ -1728,7 +1741,18 @@ int fwd_grid_t() {
 template <int LW, typename W>
 int check_grid_t() {
     static int grid = 0;
-    if (!grid) grid = persistent_grid(k_check<LW, W>, kWarps * kFwdWarpBytes);
+    if (!grid) {
+        if constexpr (sizeof(W) == 4) {
+            // two CTAs per SM (83 KB of staging buffers) and a 40 % shared-memory carveout: the
+            // rest of the SM's memory is L1 for the gathered words
+            auto kernel = k_check<LW, W>;
+            cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kWarps * kFwdWarpBytes);
+            cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 40);
+            grid = 2 * sm_count();
+        } else {
+            grid = persistent_grid(k_check<LW, W>, kWarps * kFwdWarpBytes);
+        }
+    }
     return grid;
 }
 
