@@ -342,6 +342,22 @@ def test_engine_graph_equals_eager():
     assert torch.equal(e1.delta, e2.delta) and torch.equal(e1.loss, e2.loss) and torch.equal(e1.unsat, e2.unsat)
 
 
+@pytest.mark.parametrize("dtype", ["f32", "bf16"])
+def test_engine_graph_equals_eager_owned_variables(dtype):
+    """The owned-variable pass and the 32-bit-word check (B = 32) inside a captured CUDA graph
+    reproduce the eager steps bitwise (their grids and workspaces are set up by gs_reserve)."""
+    cnf, prob = get("community")
+    B = 32
+    _abi.gs_set_tuning(prob, var_split=2, loss_mode=1)
+    e1, e2 = Engine(prob, B, dtype, seed=3), Engine(prob, B, dtype, seed=3)
+    for _ in range(5):
+        e1.step()
+    e2.run(5, graph=True)
+    torch.cuda.synchronize()
+    assert torch.equal(e1.delta, e2.delta) and torch.equal(e1.loss, e2.loss) and torch.equal(e1.unsat, e2.unsat)
+    _abi.gs_set_tuning(prob)
+
+
 def test_columns_beyond_B_untouched():
     cnf, prob = get("edge")
     n, B = cnf.n_vars, 13
