@@ -45,7 +45,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle sample")
     ap.add_argument("--no-autotune", action="store_true", help="skip gs_autotune (use defaults / --var-* flags)")
-    ap.add_argument("--legs", default="st,pool,precision,tseitin,plain,structured",
+    ap.add_argument("--legs", default="st,pool,precision,tseitin,plain,structured,batching",
                     help="extra single-GPU measurements added to the line under 'legs' (comma list of st, pool, "
                          "precision, tseitin, plain, structured, batching; 'none' for none)")
     ap.add_argument("--leg-steps", type=int, default=50, help="timed steps of each extra leg")
@@ -66,6 +66,60 @@ def workload_setup(name, dtype_override=None, scale=1.0):
     cnf = synth.workload_cnf(name, seed=0, scale=scale)
     dtype = dtype_override or w["dtype"]
     return cnf, int(w["B"]), dtype, w["desc"]
+
+
+def kernel_source_hash():
+    """sha256 of the sources the variable-major pass is compiled from: a traffic figure taken
+    by ncu is only reported while these are unchanged."""
+    import hashlib
+
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2603_28796_b300", "csrc")
+    for name in ("gs_kernels.cu", "gs_device.cuh", "gs_internal.h"):
+        with open(os.path.join(csrc, name), "rb") as f:
+            h.update(name.encode() + b"\0" + f.read())
+    return h.hexdigest()
+
+
+def recorded_traffic(workload, B, dtype):
+    """DRAM read+write bytes of one launch of the variable pass from the committed ncu summary,
+    or None when it was taken on another workload or an older kernel source."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "var_pass_traffic.json")) as f:
+            tr = json.load(f)
+    except Exception:
+        return None, None
+    if tr.get("workload") != workload or tr.get("B") != B or tr.get("dtype") != dtype:
+        return None, "recorded for another workload"
+    if tr.get("source_sha256") != kernel_source_hash():
+        return None, "recorded on an older kernel source"
+    return tr.get("bytes_per_launch"), "ncu capture (profiles/var_pass_traffic.json)"
+
+
+def gather_probe(torch, x, row_bytes, n_gathers, reps=5, seed=0):
+    """Random row-gather rate (GB/s) of the memory hierarchy for rows of row_bytes at the row
+    stride of x (a [n, ldB] tensor), the rows being drawn uniformly from all n rows: the working
+    set of one candidate chunk of the variable pass. Uses the library's probe kernel."""
+    from paper_2603_28796_b300 import _abi
+
+    n = x.shape[0]
+    g = torch.Generator(device="cpu")
+    g.manual_seed(seed)
+    idx = torch.randint(0, n, (n_gathers,), generator=g, dtype=torch.int32).to(x.device)
+    base = x.as_strided((n, x.stride(0)), (x.stride(0), 1))
+    sink = torch.zeros(1, dtype=torch.int32, device=x.device)
+    for _ in range(2):
+        _abi.gs_gather_probe(base, row_bytes, idx, sink)
+    torch.cuda.synchronize()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(reps):
+        _abi.gs_gather_probe(base, row_bytes, idx, sink)
+    b.record()
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b) / reps
+    return n_gathers * row_bytes / (ms / 1000.0) / 1e9, ms
 
 
 def measured_peaks():
@@ -201,6 +255,12 @@ def _gather_model_bytes(nnz, n, B, s):
     return nnz * B * 2 * s + n * B * (24 + s)
 
 
+def _compulsory_bytes(n, B, s):
+    """Strict DRAM floor of one fused step: delta, m, v read and written, x read once and
+    written once, the bit rows written (index data excluded)."""
+    return n * B * (24 + 2 * s) + n * ((B + 63) // 64) * 8
+
+
 def leg_precision(torch, args, peak):
     """Mixed-width power-law workload: BF16 storage (the batched form) vs FP32 (the plain form)
     on the same GPU, and the gradient error of the BF16 storage against the FP32 one at the same
@@ -217,9 +277,11 @@ def leg_precision(torch, args, peak):
         eng = Engine(prob, B, dtype, seed=11)
         ms, step_ms = _timed_steps(torch, eng, args.leg_steps, args.warmup)
         gm = _gather_model_bytes(nnz, B=B, n=n, s=s)
+        cb = _compulsory_bytes(n, B, s)
         out[dtype] = {"ms_per_step": ms, "steps_per_s": 1000.0 / ms, "evals_per_s": nnz * B / (ms / 1000.0),
                       "gs_step_ms": step_ms, "gather_model_GBps": gm / (step_ms / 1000.0) / 1e9,
-                      "gather_model_frac": gm / (step_ms / 1000.0) / 1e9 / peak, "tuning": tuning}
+                      "gather_model_frac": gm / (step_ms / 1000.0) / 1e9 / peak,
+                      "compulsory_frac": cb / (step_ms / 1000.0) / 1e9 / peak, "tuning": tuning}
         del eng
         torch.cuda.empty_cache()
     out["bf16_speedup"] = out["f32"]["ms_per_step"] / out["bf16"]["ms_per_step"]
@@ -285,10 +347,12 @@ def leg_structured(torch, args, peak):
     ms, step_ms = _timed_steps(torch, eng, args.leg_steps, args.warmup)
     s = 2
     gm = _gather_model_bytes(cnf.nnz, cnf.n_vars, B, s)
+    cb = _compulsory_bytes(cnf.n_vars, B, s)
     out = {"workload": desc, "n": cnf.n_vars, "m": cnf.n_clauses, "nnz": cnf.nnz, "B": B, "dtype": dtype,
            "ms_per_step": ms, "steps_per_s": 1000.0 / ms, "evals_per_s": cnf.nnz * B / (ms / 1000.0),
            "gs_step_ms": step_ms, "gather_model_GBps": gm / (step_ms / 1000.0) / 1e9,
-           "gather_model_frac": gm / (step_ms / 1000.0) / 1e9 / peak, "tuning": tuning}
+           "gather_model_frac": gm / (step_ms / 1000.0) / 1e9 / peak,
+           "compulsory_frac": cb / (step_ms / 1000.0) / 1e9 / peak, "tuning": tuning}
     del eng
     prob.close()
     torch.cuda.empty_cache()
@@ -309,6 +373,7 @@ def leg_batching(torch, args, peak):
     nnz, n = int(batch.clause_ptr[-1]), int(sum(batch.n_vars))
     ms, step_ms = _timed_steps(torch, eng, max(5, args.leg_steps // 5), args.warmup)
     gm = _gather_model_bytes(nnz, n, B, 4)
+    cb = _compulsory_bytes(n, B, 4)
     # the whole iteration loop captured in one CUDA graph
     Kg = max(4, (args.leg_steps // 5) // 2 * 2)
     graph = eng.capture(Kg)
@@ -324,7 +389,7 @@ def leg_batching(torch, args, peak):
     out = {"workload": desc, "n": n, "m": int(sum(batch.n_clauses)), "nnz": nnz, "B": B, "dtype": dtype,
            "batched": {"ms_per_step": ms, "steps_per_s": 1000.0 / ms, "evals_per_s": nnz * B / (ms / 1000.0),
                        "gs_step_ms": step_ms, "gather_model_frac": gm / (step_ms / 1000.0) / 1e9 / peak,
-                       "tuning": tuning},
+                       "compulsory_frac": cb / (step_ms / 1000.0) / 1e9 / peak, "tuning": tuning},
            "batched_graph": {"ms_per_step": ms_graph, "steps_per_s": 1000.0 / ms_graph,
                              "evals_per_s": nnz * B / (ms_graph / 1000.0), "steps": Kg}}
     # per-instance loop over the same state rows
@@ -613,31 +678,55 @@ def run_native(args):
     best = {"unsat": b_unsat, "rank": b_rank, "candidate": b_cand, "of": B * world}
 
     value = evals_per_step * K * world / (total_ms / 1000.0)
-    # roofline of the dominant kernel (fused variable-major pass inside gs_step)
+    # launches per step: the variable pass and its two loss-reduction kernels, the check and its
+    # two count-reduction kernels (+ the bit-row compaction for B <= 32, + the forward pass and
+    # its two reduction kernels when the loss comes from a separate pass)
+    launches_per_step = 6 + (1 if B <= 32 else 0) + (3 if tuning["loss_mode"] == 2 else 0)
+    # Roofline of the dominant kernel (the fused variable-major pass inside gs_step). The HBM
+    # fraction counts the compulsory bytes of a launch (state streams, the relaxed values read
+    # once and written once, the bit rows, the index data once per candidate chunk): the bytes
+    # that must cross HBM whatever the gather strategy. The gather model (each literal value
+    # read twice per step) counts row reads that L2 serves; it is reported under its own key and,
+    # as actual row reads, against the random-row gather rate the probe kernel measures on the
+    # same rows.
     peak, peak_kind = measured_peaks()
     lanes = tuning["var_lanes"]
-    n_chunks = -(-B // (lanes * (16 // s_bytes)))
-    compulsory = n * B * (24 + 2 * s_bytes) + n * ((B + 63) // 64) * 8 + n_chunks * 4 * (
-        info["n_occ_codes"] + info["n_var_tiles"] * 16)
-    gather_model = nnz * B * 2 * s_bytes + n * B * (24 + s_bytes)
+    vec = 16 // s_bytes
+    n_chunks = -(-B // (min(lanes, max(4, -(-B // vec))) * vec))
+    index_bytes = n_chunks * 4 * (info["n_occ_codes"] + info["n_var_tiles"] * 16)
+    compulsory = _compulsory_bytes(n, B, s_bytes) + index_bytes
+    gather_model = _gather_model_bytes(nnz, n, B, s_bytes)
     mean_step_s = statistics.mean(step_ms) / 1000.0
-    achieved = gather_model / mean_step_s / 1e9
-    traffic = None
-    try:
-        with open(os.path.join(ROOT, "profiles", "var_pass_traffic.json")) as f:
-            tr = json.load(f)
-        if tr.get("workload") == args.workload and tr.get("B") == B and tr.get("dtype") == dtype:
-            traffic = tr.get("bytes_per_launch")
-    except Exception:
-        traffic = None
+    achieved = compulsory / mean_step_s / 1e9
+    traffic, traffic_src = recorded_traffic(args.workload, B, dtype)
+    row_reads = info["n_occ_codes"] * B * s_bytes          # every occurrence code reads one row slice
+    l2 = None
+    if rank == 0:
+        row_bytes = min(512, -(-B // vec) * 16) if B * s_bytes >= 16 else 16
+        row_bytes = 1 << (int(row_bytes) - 1).bit_length()
+        probe_gbs, probe_ms = gather_probe(torch, eng.x[eng.cur], row_bytes, int(info["n_occ_codes"]))
+        kern_gbs = row_reads / mean_step_s / 1e9
+        l2 = {"row_read_bytes": row_reads, "GBps": kern_gbs, "probe_GBps": probe_gbs,
+              "frac": kern_gbs / probe_gbs, "row_bytes": row_bytes,
+              "probe": "gs_gather_probe: %d random %d-byte row reads over all %d rows at the pass's row stride "
+                       "(one candidate chunk's working set), 8 in flight per lane" % (
+                           int(info["n_occ_codes"]), row_bytes, n)}
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": traffic, "peak_source": peak_kind,
                 "kernel": "k_var_pass (fused gradient + Adam + relax + round + loss credit), timed as the gs_step call",
-                "model": "gather model: nnz*B*2s + n*B*(24+s) bytes per step (each literal value read once in "
-                         "forward and once in backward, state streamed once)",
-                "bytes_per_launch": gather_model,
-                "compulsory_bytes": compulsory, "compulsory_GBps": compulsory / mean_step_s / 1e9,
-                "compulsory_frac": compulsory / mean_step_s / 1e9 / peak,
+                "model": "compulsory bytes per launch: n*B*(24+2s) state and value streams + bit rows + index data "
+                         "once per candidate chunk",
+                "bytes_per_launch": compulsory,
+                "dram_measured": None if traffic is None else {
+                    "bytes_per_launch": traffic, "GBps": traffic / mean_step_s / 1e9,
+                    "frac": traffic / mean_step_s / 1e9 / peak, "over_compulsory": traffic / compulsory,
+                    "source": traffic_src},
+                "traffic_note": traffic_src,
+                "gather_model": {"bytes_per_launch": gather_model, "GBps": gather_model / mean_step_s / 1e9,
+                                 "frac_of_hbm_peak": gather_model / mean_step_s / 1e9 / peak,
+                                 "note": "each literal value read once in forward and once in backward; most of "
+                                         "these row reads are L2 hits, so this exceeds 1 of HBM"},
+                "l2_gather": l2,
                 "gs_step_ms": statistics.mean(step_ms), "check_ms": statistics.mean(check_ms)}
 
     cpu = None
@@ -650,10 +739,12 @@ def run_native(args):
     e2e = None
     if not args.no_e2e:
         # End to end through the public API with host buffers: every step copies that step's
-        # candidate logits from pinned host memory to the device, runs the step and the check,
-        # and reads back the per-candidate loss and unsat counts into pinned host memory. The
-        # copy of step k + 1's logits runs on a second stream into a second buffer while step k
-        # computes (the copy waits only for the step that last used that buffer).
+        # candidate logits delta from pinned host memory to the device, relaxes them to the
+        # step's input values x = sigma(delta) (gs_relax), runs the fused step on them (gradient
+        # at x, Adam on the copied delta) and the check, and reads back the per-candidate loss
+        # and unsat counts into pinned host memory. The copy of step k + 1's logits runs on a
+        # second stream into a second buffer while step k computes (the copy waits only for the
+        # step that last used that buffer).
         Ke = max(3, min(K, 20))
         host_delta = torch.from_numpy(synth.init_delta(n, B, seed=77 + rank)).pin_memory()
         host_loss = torch.empty((1, B), dtype=torch.float64).pin_memory()
@@ -681,6 +772,7 @@ def run_native(args):
                     copied[cur ^ 1].record(copy_stream)
             main.wait_event(copied[cur])
             eng.delta = dbuf[cur]
+            _abi.gs_relax(prob, eng.delta, eng.x[eng.cur])
             eng.step()
             used[cur].record(main)
             host_loss.copy_(eng.loss, non_blocking=True)
@@ -693,6 +785,8 @@ def run_native(args):
         e2e = {"value": evals_per_step * Ke * world / (e_ms / 1000.0), "unit": "evals/s",
                "h2d_bytes_per_step": n * B * 4, "d2h_bytes_per_step": B * 8 + B * 4, "steps": Ke,
                "h2d_GBps": n * B * 4 * Ke / (e_ms / 1000.0) / 1e9,
+               "inputs": "each step's logits delta [n, B] float32 copied in, relaxed on the device, stepped; "
+                         "loss [B] float64 and unsat [B] int32 copied out",
                "overlap": "copy of step k+1's inputs on a second stream during step k"}
 
     legs = None
@@ -711,7 +805,7 @@ def run_native(args):
                    "l2": "inputs larger than L2: x %.0f MB + delta/m/v %.0f MB per step" % (
                        n * B * s_bytes / 1e6, n * B * 12 / 1e6),
                    "steps_per_s": 1000.0 * K / total_ms, "tuning": tuning, "best_after_run": best},
-        "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "gpu_launches": 6 * K,
+        "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "gpu_launches": launches_per_step * K,
         "legs": legs,
     }
     if rank == 0:

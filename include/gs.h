@@ -71,6 +71,10 @@ typedef struct {
     int64_t n_var_tiles;  /* occurrence tiles (backward, fused step) */
     int64_t n_split;      /* variables whose occurrences are split over several tiles */
     int64_t device_bytes; /* index structures held on the device */
+    int32_t fwd_tile_codes;  /* tile caps the problem was built with (gs_plan_opts) */
+    int32_t var_tile_codes;
+    int32_t own_item_codes;
+    int32_t reserved;
 } gs_info;
 
 /* Adam hyper-parameters on delta. Defaults (gs_adam_default): lr 1.0, beta1 0.9, beta2 0.999,
@@ -119,6 +123,32 @@ gs_status gs_load_cnf(int64_t n_vars, int64_t n_clauses, const int64_t* clause_p
  */
 gs_status gs_load_batch(int32_t n_inst, const int64_t* n_vars, const int64_t* n_clauses, const int64_t* clause_ptr,
                         const int32_t* lits, gs_stream stream, gs_problem** out);
+
+/*
+ * gs_plan_opts - tile sizes of the index structures (a tuning knob of the kernels' work items,
+ * fixed when a problem is built; 0 takes the default).
+ *   fwd_tile_codes  literal codes per clause tile (forward pass, check): 32..512, default 512.
+ *   var_tile_codes  occurrence codes per occurrence tile (backward, fused step): 32..384,
+ *                   default 384; a variable with more codes is split over several tiles.
+ *   own_item_codes  target codes per owned-variable work item: 256..65536, default 4096.
+ *   reserved        must be 0.
+ * A tile always holds at least one whole clause / occurrence. Results differ between tilings only
+ * in the float32 summation order of the loss.
+ */
+typedef struct {
+    int32_t fwd_tile_codes;
+    int32_t var_tile_codes;
+    int32_t own_item_codes;
+    int32_t reserved;
+} gs_plan_opts;
+
+/*
+ * gs_load_batch_opts - gs_load_batch with explicit tile sizes (opts may be NULL: defaults).
+ * Errors: as gs_load_batch, plus GS_ERR_INVALID_ARG for caps out of range.
+ */
+gs_status gs_load_batch_opts(int32_t n_inst, const int64_t* n_vars, const int64_t* n_clauses,
+                             const int64_t* clause_ptr, const int32_t* lits, const gs_plan_opts* opts,
+                             gs_stream stream, gs_problem** out);
 
 /*
  * gs_load_dimacs - gs_load_cnf from a DIMACS CNF text file (header "p cnf n m", clauses
@@ -233,19 +263,21 @@ gs_status gs_forward(gs_problem* prob, const void* x, gs_dtype dtype, int32_t B,
  * runs while another component is capturing or replaying work on the device, or a latency-bound
  * loop that cannot afford the device-wide synchronisation an allocation may cause. gs_forward
  * may grow the problem's workspace on first use; this variant never allocates or frees memory.
- * (The paper has no counterpart: this is an operational variant of the forward of Eq. 2 + Eq. 5.)
- *   Arguments, output and arithmetic are those of gs_forward; results are identical.
- *   Scratch: a fixed 16 MiB device array inside the library (plus a 256-byte counter), present
- *   on every GPU that loads the library until the process exits. It holds the per-tile partial
- *   sums, n_fwd_tiles (gs_info) x Bpad x 4 bytes, where Bpad is B rounded up to the candidate
- *   chunk: a multiple of 128 (float32) or 256 (16-bit) once B exceeds that, else the next power
- *   of two of at least 16 (float32) or 32 (16-bit). Larger requests are rejected with
- *   GS_ERR_UNSUPPORTED and a message.
+ * The paper has no counterpart: this is an operational variant of gs_forward.
+ *   Arguments and output are those of gs_forward. It runs gs_forward's kernels with the same
+ *   chunking (the problem's tuned lanes per chunk) and the same two-stage reduction order, so
+ *   its results are bitwise those of gs_forward on the same problem, tuning and input.
+ *   Scratch: a fixed device array inside the library, present on every GPU that loads the
+ *   library until the process exits: 16 MiB of per-tile partial sums, n_fwd_tiles (gs_info) x
+ *   Bpad x 4 bytes (Bpad: B rounded up to the candidate chunk, at most 128 float32 / 256 16-bit
+ *   candidates per chunk), 4 MiB of stage-1 sums (reduction segments x instances x B x 8 bytes;
+ *   at most 256 segments of at least 32 tiles each), and a 256-byte counter block. Larger
+ *   requests are rejected with GS_ERR_UNSUPPORTED and a message naming the limit.
  *   The first call on a device looks up the array's device address (with that device current);
  *   make that first call before any stream capture. All calls on a device share the array and
  *   leave their partials in it: calls that overlap on the GPU (other streams, other problems,
  *   other host threads) race and must be serialised by the caller.
- * Errors: as gs_forward, plus GS_ERR_UNSUPPORTED when the partials exceed the scratch.
+ * Errors: as gs_forward, plus GS_ERR_UNSUPPORTED when the request exceeds the scratch.
  */
 gs_status gs_forward_noalloc(gs_problem* prob, const void* x, gs_dtype dtype, int32_t B, int64_t ldB, double* loss,
                              gs_stream stream);
@@ -395,6 +427,22 @@ gs_status gs_pool_sample(gs_problem* prob, const float* delta, int64_t stride, i
                          gs_stream stream);
 gs_status gs_branch_vars(gs_problem* prob, const float* delta, int64_t stride, int32_t n_rows, int32_t d,
                          int32_t* vars, gs_stream stream);
+
+/*
+ * gs_gather_probe - measurement kernel for the roofline of the variable-major pass (the K7 probe
+ * of the measurement plan; no counterpart in the paper): n_gathers random row reads of row_bytes
+ * bytes each, 16 bytes per lane, row_bytes / 16 lanes per row, 8 reads in flight per lane, with
+ * the same L2 eviction hint as the pass's gathers. Row k is at src + idx[k] * row_stride; an
+ * index >= n_rows is skipped (no read). The loaded words are folded into *sink (XOR, one atomic
+ * per warp) so that the reads are not removed. Time it with events to get the random-row gather
+ * rate of the memory hierarchy at that row size and working set (n_rows x row_bytes).
+ *   src   device, 16-byte aligned, n_rows rows of row_stride bytes (input, read only).
+ *   idx   device uint32 [n_gathers] (input).   sink  device uint32 [1] (in/out).
+ *   row_bytes a power of two in 16..512; row_stride a multiple of 16, >= row_bytes.
+ * Errors: GS_ERR_INVALID_ARG (sizes, null, alignment), GS_ERR_CUDA.
+ */
+gs_status gs_gather_probe(const void* src, int64_t n_rows, int64_t row_stride, int32_t row_bytes, const uint32_t* idx,
+                          int64_t n_gathers, uint32_t* sink, gs_stream stream);
 
 /*
  * gs_wait_selftest - exercises the device-side failure path: one warp waits on a barrier phase

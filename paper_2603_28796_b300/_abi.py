@@ -26,10 +26,10 @@ STATUS_NAMES = {
 
 # Every symbol include/gs.h declares.
 EXPORTED = (
-    "gs_adam_default", "gs_load_cnf", "gs_load_batch", "gs_load_dimacs", "gs_inspect_cnf", "gs_info_get",
+    "gs_adam_default", "gs_load_cnf", "gs_load_batch", "gs_load_batch_opts", "gs_load_dimacs", "gs_inspect_cnf", "gs_info_get",
     "gs_set_tuning", "gs_get_tuning", "gs_autotune", "gs_reserve", "gs_relax", "gs_forward", "gs_forward_noalloc", "gs_backward", "gs_step", "gs_round_check", "gs_check_bits",
     "gs_st_noise", "gs_st_sample", "gs_st_step", "gs_tseitin3", "gs_pool_sample", "gs_branch_vars",
-    "gs_wait_selftest", "gs_sync_status", "gs_free", "gs_status_str", "gs_last_error",
+    "gs_gather_probe", "gs_wait_selftest", "gs_sync_status", "gs_free", "gs_status_str", "gs_last_error",
 )
 
 
@@ -48,10 +48,17 @@ class GsInfo(ctypes.Structure):
         ("n_unit", ctypes.c_int64), ("n_taut", ctypes.c_int64), ("n_dup", ctypes.c_int64),
         ("n_occ_codes", ctypes.c_int64), ("n_fwd_tiles", ctypes.c_int64), ("n_var_tiles", ctypes.c_int64),
         ("n_split", ctypes.c_int64), ("device_bytes", ctypes.c_int64),
+        ("fwd_tile_codes", ctypes.c_int32), ("var_tile_codes", ctypes.c_int32), ("own_item_codes", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
     ]
 
     def as_dict(self) -> dict:
         return {name: int(getattr(self, name)) for name, _ in self._fields_}
+
+
+class GsPlanOpts(ctypes.Structure):
+    _fields_ = [("fwd_tile_codes", ctypes.c_int32), ("var_tile_codes", ctypes.c_int32),
+                ("own_item_codes", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class GsTuning(ctypes.Structure):
@@ -91,6 +98,7 @@ def lib():
             "gs_adam_default": (None, [ctypes.POINTER(GsAdam)]),
             "gs_load_cnf": (ctypes.c_int, [i64, i64, vp, vp, vp, pp]),
             "gs_load_batch": (ctypes.c_int, [i32, vp, vp, vp, vp, vp, pp]),
+            "gs_load_batch_opts": (ctypes.c_int, [i32, vp, vp, vp, vp, ctypes.POINTER(GsPlanOpts), vp, pp]),
             "gs_load_dimacs": (ctypes.c_int, [cp, vp, pp]),
             "gs_inspect_cnf": (ctypes.c_int, [i64, i64, vp, vp, ctypes.POINTER(GsInfo)]),
             "gs_info_get": (ctypes.c_int, [vp, ctypes.POINTER(GsInfo)]),
@@ -113,6 +121,7 @@ def lib():
             "gs_st_sample": (ctypes.c_int, [vp, vp, vp, ctypes.c_uint64, i64, i32, i64, vp, vp]),
             "gs_st_step": (ctypes.c_int, [vp, vp, vp, vp, vp, vp, vp, vp, vp, ctypes.c_uint64, i64, i32, i64,
                                           ctypes.POINTER(GsAdam), vp]),
+            "gs_gather_probe": (ctypes.c_int, [vp, i64, i64, i32, vp, i64, vp, vp]),
             "gs_wait_selftest": (ctypes.c_int, [vp, ctypes.c_uint32, vp]),
             "gs_sync_status": (ctypes.c_int, [vp]),
             "gs_free": (None, [vp]),
@@ -248,6 +257,19 @@ def gs_load_batch(n_vars, n_clauses, clause_ptr, lits, stream=None) -> Problem:
     out = ctypes.c_void_p()
     _check(lib().gs_load_batch(nv.size, _np_ptr(nv), _np_ptr(nc), _np_ptr(cp), _np_ptr(lt) if lt.size else None,
                                _stream(stream), ctypes.byref(out)), "gs_load_batch")
+    return Problem(out.value)
+
+
+def gs_load_batch_opts(n_vars, n_clauses, clause_ptr, lits, fwd_tile_codes: int = 0, var_tile_codes: int = 0,
+                       own_item_codes: int = 0, stream=None) -> Problem:
+    """gs_load_batch with explicit tile sizes (0 = default); a single formula is a batch of one."""
+    nv = np.atleast_1d(np.ascontiguousarray(n_vars, dtype=np.int64))
+    nc = np.atleast_1d(np.ascontiguousarray(n_clauses, dtype=np.int64))
+    cp, lt = _csr(clause_ptr, lits)
+    opts = GsPlanOpts(int(fwd_tile_codes), int(var_tile_codes), int(own_item_codes), 0)
+    out = ctypes.c_void_p()
+    _check(lib().gs_load_batch_opts(nv.size, _np_ptr(nv), _np_ptr(nc), _np_ptr(cp), _np_ptr(lt) if lt.size else None,
+                                    ctypes.byref(opts), _stream(stream), ctypes.byref(out)), "gs_load_batch_opts")
     return Problem(out.value)
 
 
@@ -487,6 +509,23 @@ def gs_branch_vars(prob: Problem, delta, b: int, d: int, n_rows=None, stream=Non
     out = _torch().empty(int(d), dtype=_torch().int32, device=delta.device)
     _check(lib().gs_branch_vars(prob.handle, ptr, stride, nr, int(d), _ptr(out), _stream(stream)), "gs_branch_vars")
     return out
+
+
+def gs_gather_probe(src, row_bytes: int, idx, sink=None, stream=None):
+    """Random row gathers (measurement kernel): ``src`` is a 2-D device tensor whose rows are read
+    ``row_bytes`` bytes at a time from column 0 (row stride = its row stride in bytes), ``idx``
+    a device int32/uint32 tensor of row indices; returns the uint32 sink tensor."""
+    torch = _torch()
+    if src.dim() != 2 or src.stride(1) != 1:
+        raise ValueError("src must be a 2-D tensor with unit column stride")
+    if idx.dtype not in (torch.int32,) or not idx.is_contiguous():
+        raise ValueError("idx must be a contiguous int32 tensor")
+    if sink is None:
+        sink = torch.zeros(1, dtype=torch.int32, device=src.device)
+    stride = src.stride(0) * src.element_size()
+    _check(lib().gs_gather_probe(_ptr(src), int(src.shape[0]), int(stride), int(row_bytes), _ptr(idx),
+                                 int(idx.numel()), _ptr(sink), _stream(stream)), "gs_gather_probe")
+    return sink
 
 
 def gs_wait_selftest(prob: Problem, limit_us: int = 1000, stream=None) -> None:

@@ -22,7 +22,7 @@ LIB = os.path.join(HERE, "libgaloissat.so")
 SYNTH = os.path.join(HERE, "libgs_synth.so")
 BUILD_DIR = os.path.join(HERE, "_build")
 
-CUDA_SOURCES = ["gs_host.cu", "gs_kernels.cu", "gs_st.cu", "gs_pool.cu", "gs_plan.cpp"]
+CUDA_SOURCES = ["gs_host.cu", "gs_kernels.cu", "gs_st.cu", "gs_pool.cu", "gs_probe.cu", "gs_plan.cpp"]
 CUDA_HEADERS = ["gs_internal.h", "gs_plan.h", "gs_device.cuh", "gs_noise.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -3,6 +3,7 @@
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
 #include <cmath>
@@ -32,6 +33,15 @@ gs_status fail(gs_status st, const std::string& msg) {
 gs_status cuda_fail(cudaError_t e, const char* what) {
     return fail(GS_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
 }
+
+// NVTX range around one entry point's host work and launches (header-only NVTX 3: without a
+// profiler attached a push/pop is a check of one pointer).
+struct Phase {
+    explicit Phase(const char* name) { nvtxRangePushA(name); }
+    ~Phase() { nvtxRangePop(); }
+    Phase(const Phase&) = delete;
+    Phase& operator=(const Phase&) = delete;
+};
 
 #define GS_CUDA(call, what)                                  \
     do {                                                     \
@@ -265,16 +275,31 @@ AdamK adam_consts(const gs_adam& a, int64_t t) {
 gs_status build(int32_t n_inst, const int64_t* n_vars, const int64_t* n_clauses, const int64_t* clause_ptr,
                 const int32_t* lits, HostPlan& P) {
     std::string err;
+    // the caps (set by the caller in P.caps) must stay within the kernels' staging buffers
+    if (P.caps.fwd_codes < 32 || P.caps.fwd_codes > kFwdCodes || P.caps.var_codes < 32 ||
+        P.caps.var_codes > kVarCodes || P.caps.own_codes < 256 || P.caps.own_codes > 65536)
+        return fail(GS_ERR_INVALID_ARG, "tile caps out of range (clause tiles 32..512, occurrence tiles 32..384, "
+                                        "owned items 256..65536 codes)");
     const gs_status st = build_plan(n_inst, n_vars, n_clauses, clause_ptr, lits, P, &err);
     return st == GS_OK ? GS_OK : fail(st, err);
 }
 
 gs_status load(int32_t n_inst, const int64_t* n_vars, const int64_t* n_clauses, const int64_t* clause_ptr,
-               const int32_t* lits, gs_stream stream, gs_problem** out) {
+               const int32_t* lits, const gs_plan_opts* opts, gs_stream stream, gs_problem** out) {
+    Phase phase__("gs_load");
     if (!out) return fail(GS_ERR_INVALID_ARG, "null out");
     *out = nullptr;
     gs_problem* p = new (std::nothrow) gs_problem();
     if (!p) return fail(GS_ERR_OOM, "host allocation");
+    if (opts) {
+        if (opts->reserved != 0) {
+            delete p;
+            return fail(GS_ERR_INVALID_ARG, "gs_plan_opts.reserved must be 0");
+        }
+        if (opts->fwd_tile_codes) p->h.caps.fwd_codes = opts->fwd_tile_codes;
+        if (opts->var_tile_codes) p->h.caps.var_codes = opts->var_tile_codes;
+        if (opts->own_item_codes) p->h.caps.own_codes = opts->own_item_codes;
+    }
     gs_status st = build(n_inst, n_vars, n_clauses, clause_ptr, lits, p->h);
     if (st != GS_OK) {
         delete p;
@@ -346,6 +371,9 @@ void fill_info(const HostPlan& H, int64_t fitems, int64_t vitems, int64_t vcodes
     o->n_var_tiles = vitems;
     o->n_split = H.n_split;
     o->device_bytes = dev_bytes;
+    o->fwd_tile_codes = H.caps.fwd_codes;
+    o->var_tile_codes = H.caps.var_codes;
+    o->own_item_codes = H.caps.own_codes;
 }
 
 int lanes_for_words(int32_t nwd) {
@@ -559,12 +587,18 @@ gs_status gs_inspect_cnf(int64_t n_vars, int64_t n_clauses, const int64_t* claus
 
 gs_status gs_load_cnf(int64_t n_vars, int64_t n_clauses, const int64_t* clause_ptr, const int32_t* lits,
                       gs_stream stream, gs_problem** out) {
-    return load(1, &n_vars, &n_clauses, clause_ptr, lits, stream, out);
+    return load(1, &n_vars, &n_clauses, clause_ptr, lits, nullptr, stream, out);
 }
 
 gs_status gs_load_batch(int32_t n_inst, const int64_t* n_vars, const int64_t* n_clauses, const int64_t* clause_ptr,
                         const int32_t* lits, gs_stream stream, gs_problem** out) {
-    return load(n_inst, n_vars, n_clauses, clause_ptr, lits, stream, out);
+    return load(n_inst, n_vars, n_clauses, clause_ptr, lits, nullptr, stream, out);
+}
+
+gs_status gs_load_batch_opts(int32_t n_inst, const int64_t* n_vars, const int64_t* n_clauses,
+                             const int64_t* clause_ptr, const int32_t* lits, const gs_plan_opts* opts,
+                             gs_stream stream, gs_problem** out) {
+    return load(n_inst, n_vars, n_clauses, clause_ptr, lits, opts, stream, out);
 }
 
 gs_status gs_load_dimacs(const char* path, gs_stream stream, gs_problem** out) {
@@ -663,6 +697,7 @@ gs_status gs_get_tuning(const gs_problem* p, gs_tuning* t) {
 }
 
 gs_status gs_autotune(gs_problem* p, int32_t B, gs_dtype dtype, gs_stream stream, gs_tuning* out) {
+    Phase phase__("gs_autotune");
     if (!p) return fail(GS_ERR_INVALID_ARG, "null problem");
     gs_status st = check_device(p);
     if (st != GS_OK) return st;
@@ -791,6 +826,7 @@ gs_status gs_autotune(gs_problem* p, int32_t B, gs_dtype dtype, gs_stream stream
 }
 
 gs_status gs_reserve(gs_problem* p, int32_t B, gs_dtype dtype) {
+    Phase phase__("gs_reserve");
     if (!p) return fail(GS_ERR_INVALID_ARG, "null problem");
     gs_status st = check_device(p);
     if (st != GS_OK) return st;
@@ -822,6 +858,7 @@ gs_status gs_reserve(gs_problem* p, int32_t B, gs_dtype dtype) {
 
 gs_status gs_relax(gs_problem* p, const float* delta, void* x, gs_dtype dtype, int32_t B, int64_t ldB, float tau,
                    gs_stream stream) {
+    Phase phase__("gs_relax");
     if (!p) return fail(GS_ERR_INVALID_ARG, "null problem");
     gs_status st;
     if ((st = check_batch(p, dtype, B, ldB)) != GS_OK) return st;
@@ -836,6 +873,7 @@ gs_status gs_relax(gs_problem* p, const float* delta, void* x, gs_dtype dtype, i
 
 gs_status gs_forward(gs_problem* p, const void* x, gs_dtype dtype, int32_t B, int64_t ldB, double* loss,
                      gs_stream stream) {
+    Phase phase__("gs_forward");
     if (!p) return fail(GS_ERR_INVALID_ARG, "null problem");
     gs_status st;
     if ((st = check_batch(p, dtype, B, ldB)) != GS_OK) return st;
@@ -874,6 +912,7 @@ gs_status gs_forward(gs_problem* p, const void* x, gs_dtype dtype, int32_t B, in
 
 gs_status gs_backward(gs_problem* p, const void* x, gs_dtype dtype, int32_t B, int64_t ldB, const double* dloss,
                       float* grad, gs_stream stream) {
+    Phase phase__("gs_backward");
     if (!p) return fail(GS_ERR_INVALID_ARG, "null problem");
     gs_status st;
     if ((st = check_batch(p, dtype, B, ldB)) != GS_OK) return st;
@@ -889,6 +928,7 @@ gs_status gs_backward(gs_problem* p, const void* x, gs_dtype dtype, int32_t B, i
 gs_status gs_step(gs_problem* p, float* delta, float* m, float* v, const float* grad, const void* x_in, void* x_out,
                   gs_dtype dtype, int32_t B, int64_t ldB, int64_t step, const gs_adam* adam, double* loss,
                   uint64_t* bits, gs_stream stream) {
+    Phase phase__("gs_step");
     if (!p) return fail(GS_ERR_INVALID_ARG, "null problem");
     gs_status st;
     if ((st = check_batch(p, dtype, B, ldB)) != GS_OK) return st;
@@ -934,6 +974,7 @@ gs_status gs_step(gs_problem* p, float* delta, float* m, float* v, const float* 
 
 gs_status gs_round_check(gs_problem* p, const float* delta, int32_t B, int64_t ldB, uint64_t* bits, int32_t* unsat,
                          int32_t* best, gs_stream stream) {
+    Phase phase__("gs_round_check");
     if (!p) return fail(GS_ERR_INVALID_ARG, "null problem");
     gs_status st;
     if ((st = check_batch(p, kF32, B, ldB)) != GS_OK) return st;
@@ -952,6 +993,7 @@ gs_status gs_round_check(gs_problem* p, const float* delta, int32_t B, int64_t l
 
 gs_status gs_check_bits(gs_problem* p, const uint64_t* bits, int32_t B, int32_t* unsat, int32_t* best,
                         gs_stream stream) {
+    Phase phase__("gs_check_bits");
     if (!p) return fail(GS_ERR_INVALID_ARG, "null problem");
     if (B < 0 || B > (1 << 30)) return fail(GS_ERR_INVALID_ARG, "B out of range");
     gs_status st;
@@ -962,6 +1004,23 @@ gs_status gs_check_bits(gs_problem* p, const uint64_t* bits, int32_t B, int32_t*
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     if ((st = ensure_ws(p, kF32, std::max(B, 1), false, s)) != GS_OK) return st;
     return launch_check_all(p, bits, B, unsat, best, s);
+}
+
+gs_status gs_gather_probe(const void* src, int64_t n_rows, int64_t row_stride, int32_t row_bytes, const uint32_t* idx,
+                          int64_t n_gathers, uint32_t* sink, gs_stream stream) {
+    Phase phase__("gs_gather_probe");
+    if (row_bytes < 16 || row_bytes > 512 || (row_bytes & (row_bytes - 1)))
+        return fail(GS_ERR_INVALID_ARG, "row_bytes must be a power of two in 16..512");
+    if (row_stride < row_bytes || (row_stride & 15)) return fail(GS_ERR_INVALID_ARG, "row_stride must be >= row_bytes and a multiple of 16");
+    if (n_rows < 0 || n_rows > 0xfffffffeLL || n_gathers < 0) return fail(GS_ERR_INVALID_ARG, "sizes out of range");
+    if (n_gathers > 0 && (!src || !idx || !sink)) return fail(GS_ERR_INVALID_ARG, "null pointer");
+    if (src && !aligned16(src)) return fail(GS_ERR_INVALID_ARG, "src is not 16-byte aligned");
+    if (idx && (reinterpret_cast<uintptr_t>(idx) & 3u)) return fail(GS_ERR_INVALID_ARG, "idx misaligned");
+    if (sink && (reinterpret_cast<uintptr_t>(sink) & 3u)) return fail(GS_ERR_INVALID_ARG, "sink misaligned");
+    GS_CUDA(launch_gather_probe(src, row_stride, static_cast<uint32_t>(n_rows), row_bytes, idx, n_gathers, sink,
+                                static_cast<cudaStream_t>(stream)),
+            "gather probe launch");
+    return GS_OK;
 }
 
 gs_status gs_wait_selftest(gs_problem* p, uint32_t limit_us, gs_stream stream) {
@@ -1009,18 +1068,21 @@ void gs_free(gs_problem* p) {
 }  // extern "C"
 
 // =============================================================================================
-// Allocation-free forward (gs_forward_noalloc). The per-tile loss partials and the work-queue
-// counter that gs_forward keeps in the problem's workspace live here in one fixed device array
-// instead, so a call never allocates. The array is shared by every call on a device and keeps
-// the last call's contents; the counter is cleared by each call and the partials are fully
-// rewritten before they are read.
+// Allocation-free forward (gs_forward_noalloc). The per-tile loss partials, the stage-1 sums
+// of the tile reduction and the work-queue counters that gs_forward keeps in the problem's
+// workspace live here in one fixed device array instead, so a call never allocates. The kernels,
+// chunking and reduction order are gs_forward's, so the results are bitwise the same. The array
+// is shared by every call on a device and keeps the last call's contents; the counters are
+// cleared by each call and the partials and stage sums are fully rewritten before they are read.
 namespace {
 
-constexpr size_t kNoAllocHeader = 256;                   // work-queue counter (int32 at offset 0)
-constexpr size_t kNoAllocPartialBytes = size_t(16) << 20; // 16 MiB of float32 tile partials
+constexpr size_t kNoAllocHeader = 256;                     // work-queue counters (two int32)
+constexpr size_t kNoAllocPartialBytes = size_t(16) << 20;  // 16 MiB of float32 tile partials
+constexpr size_t kNoAllocStageBytes = size_t(4) << 20;     // 4 MiB of float64 stage-1 sums
 constexpr int kNoAllocMaxDevices = 64;
 
-static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocHeader + kNoAllocPartialBytes];
+static __device__ __align__(256) unsigned char
+    g_noalloc_scratch[kNoAllocHeader + kNoAllocPartialBytes + kNoAllocStageBytes];
 
 // Device address of g_noalloc_scratch per device, looked up once with that device current.
 void* g_noalloc_addr[kNoAllocMaxDevices] = {};
@@ -1051,17 +1113,26 @@ extern "C" gs_status gs_forward_noalloc(gs_problem* p, const void* x, gs_dtype d
     if (loss && (reinterpret_cast<uintptr_t>(loss) & 7u)) return fail(GS_ERR_INVALID_ARG, "loss misaligned");
     if ((st = check_device(p)) != GS_OK) return st;
     if (B == 0) return GS_OK;
-    const Chunking c = chunking_for(dtype, B);
+    // the same chunking (tuned lane cap) and segment count as gs_forward
+    const Chunking c = chunking_for(dtype, B, p->fwd_lc_max);
+    const int32_t n_seg = n_segments(p, B, max_list(p->h.f_iptr));
     const size_t need = static_cast<size_t>(p->n_fitems) * static_cast<size_t>(c.bpad) * sizeof(float);
     if (need > kNoAllocPartialBytes)
         return fail(GS_ERR_UNSUPPORTED, "gs_forward_noalloc needs " + std::to_string(need) +
                                             " bytes of tile partials (clause tiles x padded B x 4); its fixed "
                                             "scratch holds 16 MiB - use gs_forward for this size");
+    const size_t need_stage = static_cast<size_t>(n_seg) * static_cast<size_t>(std::max(p->h.n_inst, 1)) *
+                              static_cast<size_t>(B) * sizeof(double);
+    if (need_stage > kNoAllocStageBytes)
+        return fail(GS_ERR_UNSUPPORTED, "gs_forward_noalloc needs " + std::to_string(need_stage) +
+                                            " bytes of stage sums (segments x instances x B x 8); its fixed "
+                                            "scratch holds 4 MiB - use gs_forward for this size");
     unsigned char* base = nullptr;
     if ((st = noalloc_scratch(p->device, &base)) != GS_OK) return st;
     int32_t* head = reinterpret_cast<int32_t*>(base);
     int32_t* exit_cnt = head + 1;
     float* part = reinterpret_cast<float*>(base + kNoAllocHeader);
+    double* stage = reinterpret_cast<double*>(base + kNoAllocHeader + kNoAllocPartialBytes);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     FwdParams fp{};
     fp.items = p->fitems;
@@ -1083,7 +1154,8 @@ extern "C" gs_status gs_forward_noalloc(gs_problem* p, const void* x, gs_dtype d
         const int grid = static_cast<int>(std::min<int64_t>(grid_forward(dtype, c.lc), total));
         GS_CUDA(launch_forward(fp, dtype, c.lc, grid, s), "forward launch");
     }
-    GS_CUDA(launch_loss_reduce(part, c.bpad, p->f_iptr, p->f_list, p->inst_empty, p->h.n_inst, B, loss, s),
+    GS_CUDA(launch_loss_reduce2(part, c.bpad, p->f_iptr, p->f_list, p->inst_empty, p->h.n_inst, B, n_seg, stage,
+                                loss, s),
             "loss reduce launch");
     return GS_OK;
 }
@@ -1101,6 +1173,7 @@ gs_status st_common(gs_problem* p, int32_t B, int64_t ldB) {
 
 gs_status gs_st_noise(gs_problem* p, uint64_t seed, int64_t step, float* noise, int32_t B, int64_t ldB,
                       gs_stream stream) {
+    Phase phase__("gs_st_noise");
     gs_status st;
     if ((st = st_common(p, B, ldB)) != GS_OK) return st;
     const bool any = p->h.n > 0 && B > 0;
@@ -1114,6 +1187,7 @@ gs_status gs_st_noise(gs_problem* p, uint64_t seed, int64_t step, float* noise, 
 
 gs_status gs_st_sample(gs_problem* p, const float* delta, const float* noise, uint64_t seed, int64_t step, int32_t B,
                        int64_t ldB, uint64_t* bits, gs_stream stream) {
+    Phase phase__("gs_st_sample");
     gs_status st;
     if ((st = st_common(p, B, ldB)) != GS_OK) return st;
     const bool any = p->h.n > 0 && B > 0;
@@ -1132,6 +1206,7 @@ gs_status gs_st_sample(gs_problem* p, const float* delta, const float* noise, ui
 gs_status gs_st_step(gs_problem* p, float* delta, float* m, float* v, const uint64_t* bits_in, uint64_t* bits_out,
                      const float* noise, const float* noise_next, float* noise_next_out, uint64_t seed, int64_t step,
                      int32_t B, int64_t ldB, const gs_adam* adam, gs_stream stream) {
+    Phase phase__("gs_st_step");
     gs_status st;
     if ((st = st_common(p, B, ldB)) != GS_OK) return st;
     if (step < 1) return fail(GS_ERR_INVALID_ARG, "step must be >= 1");
@@ -1246,6 +1321,7 @@ gs_status pool_run(gs_problem* p, const float* delta, int64_t stride, int32_t n_
 gs_status gs_pool_sample(gs_problem* p, const float* delta, int64_t stride, int32_t n_rows, const float* noise,
                          int64_t ldN, uint64_t seed, int32_t N, int32_t S, uint64_t* bits, int32_t* sel,
                          gs_stream stream) {
+    Phase phase__("gs_pool_sample");
     if (!p) return fail(GS_ERR_INVALID_ARG, "null problem");
     gs_status st;
     if ((st = need_ptr(noise, "noise", false)) != GS_OK || (st = need_ptr(bits, "bits", false)) != GS_OK) return st;
@@ -1255,6 +1331,7 @@ gs_status gs_pool_sample(gs_problem* p, const float* delta, int64_t stride, int3
 
 gs_status gs_branch_vars(gs_problem* p, const float* delta, int64_t stride, int32_t n_rows, int32_t d, int32_t* vars,
                          gs_stream stream) {
+    Phase phase__("gs_branch_vars");
     if (!p) return fail(GS_ERR_INVALID_ARG, "null problem");
     return pool_run(p, delta, stride, n_rows, nullptr, 0, 0, 1, d, true, nullptr, vars,
                     static_cast<cudaStream_t>(stream));

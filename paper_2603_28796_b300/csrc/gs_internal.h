@@ -266,9 +266,6 @@ cudaError_t launch_forward(const FwdParams& p, int dtype, int lc, int grid, cuda
 cudaError_t launch_check(const CheckParams& p, int lw, bool words32, int grid, cudaStream_t s);
 // out[v] = low 32 bits of bits[v * nwd] for v < n (the candidates 0..31 of each row).
 cudaError_t launch_compact_low32(const uint64_t* bits, int64_t n, int32_t nwd, uint32_t* out, cudaStream_t s);
-cudaError_t launch_loss_reduce(const float* part, int32_t bpad, const int32_t* inst_items_ptr,
-                               const int32_t* inst_items, const int64_t* n_empty, int32_t n_inst,
-                               int32_t B, double* loss, cudaStream_t s);
 // Two-stage fixed-order reductions over the tiles of each instance (n_seg segments in stage 1;
 // stage holds n_seg * n_inst * B values).
 cudaError_t launch_loss_reduce2(const float* part, int32_t bpad, const int32_t* iptr, const int32_t* items,
@@ -291,6 +288,10 @@ cudaError_t launch_round(const float* delta, uint32_t* bits32, int64_t n, int32_
 cudaError_t launch_adam(float* delta, float* m, float* v, const float* grad, void* x_out, int dtype,
                         int64_t n, int32_t B, int64_t ldB, const AdamK& k, cudaStream_t s);
 cudaError_t launch_wait_selftest(int32_t* status, uint64_t limit_ns, cudaStream_t s);
+// Random row gathers (gs_gather_probe): n gathers of row_bytes (16..512, a power of two) at rows
+// idx[k] < n_rows of src (row stride `stride` bytes, 16-byte aligned); XOR of the data into sink.
+cudaError_t launch_gather_probe(const void* src, int64_t stride, uint32_t n_rows, int32_t row_bytes,
+                                const uint32_t* idx, int64_t n, uint32_t* sink, cudaStream_t s);
 // Occupancy-derived persistent grid size for a tiled kernel instantiation.
 int grid_var_pass(int dtype, int mode, int lc);
 int grid_forward(int dtype, int lc);

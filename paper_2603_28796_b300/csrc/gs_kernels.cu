@@ -1616,28 +1616,6 @@ __global__ void __launch_bounds__(1024) k_count_final(const int32_t* stage, int3
 }
 
 // ------------------------------------------------------------------------------------------
-// FP64 reduction of per-tile loss partials, per instance, in tile order.
-__global__ void __launch_bounds__(256) k_loss_reduce(const float* part, int32_t bpad, const int32_t* iptr,
-                                                     const int32_t* items, const int64_t* n_empty, int32_t B,
-                                                     double* loss) {
-    __shared__ double red[8][32];
-    const int inst = blockIdx.y;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int b = blockIdx.x * 32 + lane;
-    const int a = iptr[inst], e = iptr[inst + 1];
-    double s = 0.0;
-    if (b < B)
-        for (int k = a + warp; k < e; k += 8) s += static_cast<double>(part[static_cast<int64_t>(items[k]) * bpad + b]);
-    red[warp][lane] = s;
-    __syncthreads();
-    if (warp == 0 && b < B) {
-        double t = 0.0;
-#pragma unroll
-        for (int q = 0; q < 8; ++q) t += red[q][lane];
-        loss[static_cast<int64_t>(inst) * B + b] = t + static_cast<double>(n_empty[inst]);
-    }
-}
-
 // Relaxed values x = sigma(delta / tau), written as T: one thread per 4 consecutive candidates of
 // a row (16-byte loads; the row stride keeps every group aligned), scalar tail past B.
 template <typename T>
@@ -1946,15 +1924,6 @@ cudaError_t launch_check(const CheckParams& p, int lw, bool words32, int grid, c
 cudaError_t launch_compact_low32(const uint64_t* bits, int64_t n, int32_t nwd, uint32_t* out, cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
     k_compact_low32<<<elementwise_grid(n), 256, 0, s>>>(bits, n, nwd, out);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_loss_reduce(const float* part, int32_t bpad, const int32_t* inst_items_ptr,
-                               const int32_t* inst_items, const int64_t* n_empty, int32_t n_inst, int32_t B,
-                               double* loss, cudaStream_t s) {
-    if (B <= 0 || n_inst <= 0) return cudaSuccess;
-    dim3 grid((B + 31) / 32, n_inst);
-    k_loss_reduce<<<grid, 256, 0, s>>>(part, bpad, inst_items_ptr, inst_items, n_empty, B, loss);
     return cudaGetLastError();
 }
 

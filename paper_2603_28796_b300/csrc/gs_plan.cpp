@@ -189,9 +189,8 @@ int tile_cap(int64_t count, int cap) {
     return static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(cap, want)));
 }
 
-// Clause tiles: consecutive whole clauses of one instance, <= kFwdCodes codes, <= kFwdClauses.
-// One code per literal in literal order, so a tile's codes start at its first clause's offset.
-// Clause tiles: whole clauses of one instance, <= kFwdCodes codes, <= kFwdClauses. The tiles
+// Clause tiles: whole clauses of one instance, at most caps.fwd_codes codes (<= kFwdCodes; at
+// least one clause) and kFwdClauses clauses. The tiles
 // take the clauses in the order of their median literal's variable row (a stable counting sort;
 // an empty clause keys on its instance's first row), so that a tile's literals fall on nearby
 // rows when the formula has locality (clauses of one community, chains of one long clause)
@@ -247,7 +246,7 @@ void build_fwd(const int64_t* clause_ptr, const int32_t* lits, HostPlan& P) {
             int nc = 0, ncodes = 0;
             while (t < te && nc < clause_cap) {
                 const int k = static_cast<int>(pos_code[t + 1] - pos_code[t]);
-                if (ncodes + k > kFwdCodes) break;
+                if (nc > 0 && ncodes + k > P.caps.fwd_codes) break;
                 ncodes += k;
                 ++nc;
                 ++t;
@@ -389,9 +388,10 @@ gs_status build_var(const int64_t* clause_ptr, const int32_t* lits, HostPlan& P)
             open = false;
         };
         for (int64_t v = ra; v < rb; ++v) {
-            if (cost(v) > kVarCodes) {
+            if (cost(v) > P.caps.var_codes) {
                 close_item();
-                // parts of <= kVarCodes codes, split at occurrence boundaries
+                // parts of <= var_codes codes (at least one occurrence), split at occurrence
+                // boundaries
                 const int32_t slot = P.n_split++;
                 const int32_t row0 = P.n_split_rows;
                 const size_t first_part = made.size();
@@ -413,7 +413,7 @@ gs_status build_var(const int64_t* clause_ptr, const int32_t* lits, HostPlan& P)
                     while (q < qe) {
                         int w = 1;
                         while (!(codes[q + w - 1] & kVEnd)) ++w;   // this occurrence's codes
-                        if (c + w > kVarCodes) break;
+                        if (c > 0 && c + w > P.caps.var_codes) break;
                         c += w;
                         q += w;
                         kk = combine_kk(kk, w);
@@ -432,7 +432,7 @@ gs_status build_var(const int64_t* clause_ptr, const int32_t* lits, HostPlan& P)
                 P.n_split_rows += pi;
                 continue;
             }
-            if (open && (cur.nv == var_cap || cur.n_codes + cost(v) > kVarCodes)) close_item();
+            if (open && (cur.nv == var_cap || cur.n_codes + cost(v) > P.caps.var_codes)) close_item();
             if (!open) {
                 cur = VarItem{};
                 cur.code_base = code_start[v];
@@ -524,7 +524,8 @@ gs_status build_var(const int64_t* clause_ptr, const int32_t* lits, HostPlan& P)
             vk[v] = kk;
         }
     });
-    const int64_t own_cap = std::max<int64_t>(256, std::min<int64_t>(kOwnCodes, code_start[n] / kMinTiles));
+    const int64_t own_cap =
+        std::max<int64_t>(256, std::min<int64_t>(P.caps.own_codes, code_start[n] / kMinTiles));
     P.oitems.clear();
     P.oent.clear();
     std::vector<int32_t> order;

@@ -10,7 +10,17 @@
 
 namespace gs {
 
+// Tile size caps of the builder (gs_plan_opts); each at most the compile-time buffer size of its
+// tile kind. A tile always takes at least one whole clause (occurrence), which fits any cap's
+// buffer since a clause has at most kMaxClauseWidth literals.
+struct PlanCaps {
+    int fwd_codes = kFwdCodes;     // literal codes per clause tile
+    int var_codes = kVarCodes;     // occurrence codes per occurrence tile (or split part)
+    int own_codes = kOwnCodes;     // codes per owned-variable item (target)
+};
+
 struct HostPlan {
+    PlanCaps caps;
     int64_t n = 0, m = 0, nnz = 0;
     int32_t n_inst = 0, max_k = 0;
     int64_t n_empty = 0, n_unit = 0, n_taut = 0, n_dup = 0;

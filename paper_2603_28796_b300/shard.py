@@ -1,4 +1,4 @@
-"""Candidate sharding across ranks (one process per GPU).
+"""Candidate and instance sharding across ranks (one process per GPU).
 
 Candidates are independent: a candidate's loss, gradient, update, rounding and check involve no
 other candidate (Eq. 2 and Eq. 5 are per-candidate sums; the batch objective is their sum). So
@@ -8,12 +8,16 @@ candidates (global candidate id = rank * B + b) and steps them with no per-step 
 The one exchange is at the end of a run: the ranks agree on the best candidate (fewest
 unsatisfied clauses; ties to the lowest global id, matching the single-GPU check) and the
 winning rank broadcasts its rounded assignment (Eq. 4), e.g. for the hand-off to a CPU solver.
-Everything here is host-side plumbing over ``torch.distributed``; it works with gloo on CPU
+A batch of many instances (gs_load_batch) can instead be partitioned by instance: every rank
+loads a sub-batch of whole instances, chosen so that the ranks' literal counts (the work of a
+step is proportional to nnz * B) are balanced, and steps all B candidates of each; at the end
+the ranks exchange one row per instance (fewest unsatisfied clauses and the candidate reaching
+it). Everything here is host-side plumbing over ``torch.distributed``; it works with gloo on CPU
 tensors and with NCCL on device tensors.
 """
 from __future__ import annotations
 
-from typing import Optional, Tuple
+from typing import List, Optional, Sequence, Tuple
 
 import torch
 import torch.distributed as dist
@@ -69,6 +73,88 @@ def global_best(unsat: torch.Tensor, best: torch.Tensor, bits: torch.Tensor, n: 
     src = dist.get_global_rank(group, r_best) if group is not None else r_best
     dist.broadcast(out, src=src, group=group)
     return r_best, b_best, u_best, out
+
+
+def partition_instances(nnz: Sequence[int], world: int) -> List[List[int]]:
+    """Split instances over ``world`` ranks by literal count: largest instance first, each to the
+    rank with the smallest load so far (ties to the lowest rank). Returns each rank's instance
+    ids in ascending order. Deterministic; every instance goes to exactly one rank."""
+    if world < 1:
+        raise ValueError("world must be >= 1")
+    order = sorted(range(len(nnz)), key=lambda i: (-int(nnz[i]), i))
+    load = [0] * world
+    parts: List[List[int]] = [[] for _ in range(world)]
+    for i in order:
+        r = min(range(world), key=lambda q: (load[q], q))
+        parts[r].append(i)
+        load[r] += int(nnz[i])
+    return [sorted(p) for p in parts]
+
+
+def sub_batch(n_vars, n_clauses, clause_ptr, lits, ids: Sequence[int]):
+    """The CSR arrays (n_vars, n_clauses, clause_ptr, lits) of the instances ``ids`` of a batch
+    (instance-local literals are kept; clause_ptr is rebased), ready for gs_load_batch."""
+    import numpy as np
+
+    n_vars = np.asarray(n_vars, dtype=np.int64)
+    n_clauses = np.asarray(n_clauses, dtype=np.int64)
+    c_off = np.concatenate([[0], np.cumsum(n_clauses)])
+    cps, lts = [np.zeros(1, dtype=np.int64)], []
+    base = 0
+    for i in ids:
+        c0, c1 = int(c_off[i]), int(c_off[i + 1])
+        a, b = int(clause_ptr[c0]), int(clause_ptr[c1])
+        cps.append(np.asarray(clause_ptr[c0 + 1:c1 + 1], dtype=np.int64) - a + base)
+        lts.append(np.asarray(lits[a:b], dtype=np.int32))
+        base += b - a
+    ids = list(ids)
+    return (n_vars[ids].copy(), n_clauses[ids].copy(), np.concatenate(cps),
+            np.concatenate(lts) if lts else np.zeros(0, dtype=np.int32))
+
+
+def global_best_instances(inst_ids: Sequence[int], unsat: torch.Tensor, best: torch.Tensor, n_inst: int,
+                          cand_offset: int = 0, group=None) -> torch.Tensor:
+    """Per-instance best candidate over all ranks of an instance-partitioned batch.
+
+    inst_ids: the global ids of this rank's instances (row i of unsat / best is instance
+    inst_ids[i]); unsat: [len(inst_ids), B] int32 counts; best: [len(inst_ids)] int32 lowest local
+    candidate with the fewest; cand_offset: global id of this rank's candidate 0 (0 when every
+    instance lives on one rank; rank * B when ranks also split the candidates of an instance).
+    Returns int64 [n_inst, 3] = (unsat, global candidate, rank) per instance, identical on every
+    rank: fewest unsatisfied clauses, ties to the lowest global candidate then the lowest rank;
+    (-1, -1, -1) for an instance no rank holds."""
+    rows = []
+    for i, g in enumerate(inst_ids):
+        b = int(best[i].item())
+        rows.append((int(g), int(unsat[i, b].item()), int(cand_offset) + b))
+    rank = dist.get_rank(group) if (dist.is_available() and dist.is_initialized()) else 0
+    mine = torch.tensor([[g, u, c, rank] for g, u, c in rows] or [[-1, 0, 0, 0]], dtype=torch.int64)
+    if dist.is_available() and dist.is_initialized():
+        world = dist.get_world_size(group)
+        dev = unsat.device
+        cnt = torch.tensor([mine.shape[0]], dtype=torch.int64, device=dev)
+        cnts = [torch.zeros_like(cnt) for _ in range(world)]
+        dist.all_gather(cnts, cnt, group=group)
+        mx = int(max(int(c.item()) for c in cnts))
+        pad = torch.full((mx, 4), -1, dtype=torch.int64)
+        pad[:mine.shape[0]] = mine
+        pad = pad.to(dev)
+        allv = [torch.zeros_like(pad) for _ in range(world)]
+        dist.all_gather(allv, pad, group=group)
+        table = torch.cat([a.cpu() for a in allv])
+    else:
+        table = mine
+    out = torch.full((int(n_inst), 3), -1, dtype=torch.int64)
+    best_key = {}
+    for g, u, c, r in table.tolist():
+        if g < 0:
+            continue
+        key = (u, c, r)
+        if g not in best_key or key < best_key[g]:
+            best_key[g] = key
+    for g, (u, c, r) in best_key.items():
+        out[g] = torch.tensor([u, c, r])
+    return out
 
 
 def init_from_env(backend: Optional[str] = None) -> Tuple[int, int, int]:

@@ -392,6 +392,7 @@ def test_wait_timeout_is_reported_and_context_survives():
     H.assert_loss(loss.cpu().numpy()[0], lu)
 
 
+@pytest.mark.filterwarnings("ignore:The CUDA Graph is empty")
 def test_capture_without_reserve_is_refused():
     cnf = synth.planted_ksat(200, 800, 3, seed=77)
     prob = H.load(cnf)

@@ -94,3 +94,85 @@ def test_single_process_fallbacks():
     assert (r, b, u) == (0, 66, 1) and np.array_equal(a.numpy(), x[:, 66].astype(np.uint8))
     assert shard.max_over_ranks(3.5) == 3.5
     assert len({shard.rank_seed(1, r) for r in range(8)}) == 8
+
+
+# ---------------------------------------------------------------------------------------------
+# Instance sharding of a batch of many instances: greedy split by literal count, sub-batch
+# extraction, and the per-instance best exchange.
+def test_partition_instances_covers_and_balances():
+    rng = np.random.default_rng(3)
+    nnz = rng.integers(3_000, 2_000_000, size=512)
+    for world in (1, 2, 3, 8):
+        parts = shard.partition_instances(nnz, world)
+        flat = sorted(i for p in parts for i in p)
+        assert flat == list(range(nnz.size))
+        assert all(p == sorted(p) for p in parts)
+        loads = [int(nnz[p].sum()) for p in parts]
+        # largest-first greedy: the heaviest rank exceeds the lightest by at most one instance
+        assert max(loads) - min(loads) <= int(nnz.max())
+    assert shard.partition_instances([5, 5, 5, 5], 2) == [[0, 2], [1, 3]]
+    with pytest.raises(ValueError):
+        shard.partition_instances([1], 0)
+
+
+def test_sub_batch_equals_selected_instances():
+    from paper_2603_28796_b300 import synth
+
+    parts = [synth.planted_ksat(50 + 10 * i, 200 + 40 * i, 3 + i % 2, seed=i) for i in range(5)]
+    batch = synth.concat(parts)
+    ids = [1, 3, 4]
+    nv, nc, cp, lits = shard.sub_batch(batch.n_vars, batch.n_clauses, batch.clause_ptr, batch.lits, ids)
+    ref = synth.concat([parts[i] for i in ids])
+    assert np.array_equal(nv, ref.n_vars) and np.array_equal(nc, ref.n_clauses)
+    assert np.array_equal(cp, ref.clause_ptr) and np.array_equal(lits, ref.lits)
+    nv, nc, cp, lits = shard.sub_batch(batch.n_vars, batch.n_clauses, batch.clause_ptr, batch.lits, [])
+    assert nv.size == 0 and cp.tolist() == [0] and lits.size == 0
+
+
+def _inst_case(n_inst, B, seed):
+    rng = np.random.default_rng(seed)
+    return rng.integers(2, 40, size=(n_inst, B)).astype(np.int32)
+
+
+def _inst_worker(rank, world, port, n_inst, B, out_dir):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world),
+                      LOCAL_RANK=str(rank))
+    shard.init_from_env("gloo")
+    nnz = np.arange(1, n_inst + 1) * 1000
+    ids = shard.partition_instances(nnz, world)[rank]
+    full = _inst_case(n_inst, B, 11)
+    unsat = full[ids]
+    best = torch.from_numpy(np.argmin(unsat, axis=1).astype(np.int32))
+    table = shard.global_best_instances(ids, torch.from_numpy(unsat), best, n_inst)
+    torch.save(table, os.path.join(out_dir, "i%d.pt" % rank))
+    torch.distributed.destroy_process_group()
+
+
+def test_global_best_instances_world2(tmp_path):
+    n_inst, B = 9, 70
+    ctx = mp.get_context("spawn")
+    port = _free_port()
+    procs = [ctx.Process(target=_inst_worker, args=(r, 2, port, n_inst, B, str(tmp_path))) for r in range(2)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(timeout=120)
+        assert p.exitcode == 0
+    tables = [torch.load(os.path.join(tmp_path, "i%d.pt" % r)) for r in range(2)]
+    assert torch.equal(tables[0], tables[1])
+    full = _inst_case(n_inst, B, 11)
+    owner = {}
+    for r, ids in enumerate(shard.partition_instances(np.arange(1, n_inst + 1) * 1000, 2)):
+        for i in ids:
+            owner[i] = r
+    for i in range(n_inst):
+        b = int(np.argmin(full[i]))
+        assert tables[0][i].tolist() == [int(full[i, b]), b, owner[i]]
+
+
+def test_global_best_instances_single_process_and_ties():
+    unsat = torch.tensor([[4, 2, 2], [7, 7, 1]], dtype=torch.int32)
+    best = torch.tensor([1, 2], dtype=torch.int32)
+    t = shard.global_best_instances([3, 0], unsat, best, 5, cand_offset=10)
+    assert t[3].tolist() == [2, 11, 0] and t[0].tolist() == [1, 12, 0]
+    assert t[1].tolist() == [-1, -1, -1]
