@@ -75,7 +75,7 @@ def kernel_source_hash():
 
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2603_28796_b300", "csrc")
-    for name in ("gs_kernels.cu", "gs_device.cuh", "gs_internal.h"):
+    for name in ("gs_kernels.cu", "gs_var.cuh", "gs_device.cuh", "gs_internal.h"):
         with open(os.path.join(csrc, name), "rb") as f:
             h.update(name.encode() + b"\0" + f.read())
     return h.hexdigest()
@@ -120,6 +120,18 @@ def gather_probe(torch, x, row_bytes, n_gathers, reps=5, seed=0):
     torch.cuda.synchronize()
     ms = a.elapsed_time(b) / reps
     return n_gathers * row_bytes / (ms / 1000.0) / 1e9, ms
+
+
+def load_tuned(cnf, B, dtype, search_tiles=True):
+    """The workload's problem, loaded with its tuned tile sizes and run-time settings (the
+    package's tuning cache, else a search that is then cached); returns (problem, record)."""
+    from paper_2603_28796_b300 import tuning
+
+    prob, rec = tuning.tuned_problem(cnf, B, dtype, search_tiles=search_tiles)
+    out = {"plan": rec["plan"], "tuning": rec["tuning"], "source": rec["source"]}
+    if rec.get("tried"):
+        out["tried"] = [{"plan": t["plan"], "ms_per_step": t["ms_per_step"]} for t in rec["tried"]]
+    return prob, out
 
 
 def measured_peaks():
@@ -269,11 +281,10 @@ def leg_precision(torch, args, peak):
     from paper_2603_28796_b300.engine import Engine, candidates
 
     cnf, B, _, desc = workload_setup("precision")
-    prob = _abi.gs_load_cnf(cnf.n_vars, cnf.clause_ptr, cnf.lits)
     n, nnz = cnf.n_vars, cnf.nnz
     out = {"workload": desc, "n": n, "m": cnf.n_clauses, "nnz": nnz, "B": B}
     for dtype, s in (("bf16", 2), ("f32", 4)):
-        tuning = _abi.gs_autotune(prob, B, dtype)
+        prob, tuning = load_tuned(cnf, B, dtype)
         eng = Engine(prob, B, dtype, seed=11)
         ms, step_ms = _timed_steps(torch, eng, args.leg_steps, args.warmup)
         gm = _gather_model_bytes(nnz, B=B, n=n, s=s)
@@ -283,6 +294,8 @@ def leg_precision(torch, args, peak):
                       "gather_model_frac": gm / (step_ms / 1000.0) / 1e9 / peak,
                       "compulsory_frac": cb / (step_ms / 1000.0) / 1e9 / peak, "tuning": tuning}
         del eng
+        if dtype == "bf16":
+            prob.close()
         torch.cuda.empty_cache()
     out["bf16_speedup"] = out["f32"]["ms_per_step"] / out["bf16"]["ms_per_step"]
     delta = candidates(n, B)
@@ -310,8 +323,7 @@ def leg_plain(torch, args):
     from paper_2603_28796_b300.engine import Engine
 
     cnf, B, dtype, desc = workload_setup("plain")
-    prob = _abi.gs_load_cnf(cnf.n_vars, cnf.clause_ptr, cnf.lits)
-    tuning = _abi.gs_autotune(prob, B, dtype)
+    prob, tuning = load_tuned(cnf, B, dtype)
     eng = Engine(prob, B, dtype, seed=5)
     steps = 1000
     eng.run(steps, graph=True)           # warm-up replay (capture included)
@@ -341,8 +353,7 @@ def leg_structured(torch, args, peak):
     from paper_2603_28796_b300.engine import Engine
 
     cnf, B, dtype, desc = workload_setup("structured")
-    prob = _abi.gs_load_cnf(cnf.n_vars, cnf.clause_ptr, cnf.lits)
-    tuning = _abi.gs_autotune(prob, B, dtype)
+    prob, tuning = load_tuned(cnf, B, dtype)
     eng = Engine(prob, B, dtype, seed=21)
     ms, step_ms = _timed_steps(torch, eng, args.leg_steps, args.warmup)
     s = 2
@@ -367,8 +378,7 @@ def leg_batching(torch, args, peak):
 
     bt = workload_setup("batching")
     batch, B, dtype, desc = bt
-    prob = _abi.gs_load_batch(batch.n_vars, batch.n_clauses, batch.clause_ptr, batch.lits)
-    tuning = _abi.gs_autotune(prob, B, dtype)
+    prob, tuning = load_tuned(batch, B, dtype, search_tiles=False)
     eng = Engine(prob, B, dtype, seed=31)
     nnz, n = int(batch.clause_ptr[-1]), int(sum(batch.n_vars))
     ms, step_ms = _timed_steps(torch, eng, max(5, args.leg_steps // 5), args.warmup)
@@ -445,7 +455,7 @@ def leg_tseitin(torch, args, peak):
     """The paper's formulation vs the native one on the mixed-width power-law formula (FP32,
     B = 256): the width-3 chain normalisation of Eq. 6-8 (gs_tseitin3: more variables and
     clauses, every clause of width 3) against the formula with its own clause widths."""
-    from paper_2603_28796_b300 import _abi
+    from paper_2603_28796_b300 import _abi, synth
     from paper_2603_28796_b300.engine import Engine
 
     cnf, B, _, desc = workload_setup("precision")
@@ -453,8 +463,7 @@ def leg_tseitin(torch, args, peak):
     out = {"workload": desc.replace("BF16 storage vs FP32", "FP32") + "; native widths vs width-3 chains (Eq. 6-8)",
            "B": B}
     for name, (n, cp, lits) in (("native", (cnf.n_vars, cnf.clause_ptr, cnf.lits)), ("width3", (n3, cp3, lits3))):
-        prob = _abi.gs_load_cnf(n, cp, lits)
-        tuning = _abi.gs_autotune(prob, B, "f32")
+        prob, tuning = load_tuned(synth.CNF(n, cp, lits), B, "f32", search_tiles=False)
         eng = Engine(prob, B, "f32", seed=13)
         ms, step_ms = _timed_steps(torch, eng, args.leg_steps, args.warmup)
         nnz = int(cp[-1])
@@ -625,12 +634,13 @@ def run_native(args):
     cnf, B, dtype, desc = workload_setup(args.workload, args.dtype, args.scale)
     if args.scale != 1.0:
         desc += " (formula scaled by %g: n=%d, m=%d)" % (args.scale, cnf.n_vars, cnf.n_clauses)
-    prob = _abi.gs_load_cnf(cnf.n_vars, cnf.clause_ptr, cnf.lits)
-    if args.var_lanes or args.var_gather or args.var_split or args.loss_mode:
+    tune_rec = None
+    if args.var_lanes or args.var_gather or args.var_split or args.loss_mode or args.no_autotune:
+        prob = _abi.gs_load_cnf(cnf.n_vars, cnf.clause_ptr, cnf.lits)
         _abi.gs_set_tuning(prob, var_lanes=args.var_lanes, var_gather=args.var_gather, var_split=args.var_split,
                            loss_mode=args.loss_mode)
-    elif not args.no_autotune:
-        _abi.gs_autotune(prob, B, dtype)
+    else:
+        prob, tune_rec = load_tuned(cnf, B, dtype)
     tuning = _abi.gs_get_tuning(prob)
     info = prob.info()
     eng = Engine(prob, B, dtype, seed=shard.rank_seed(1, rank))
@@ -804,7 +814,9 @@ def run_native(args):
                    "parallelism": "dp%d (independent candidate batches)" % world,
                    "l2": "inputs larger than L2: x %.0f MB + delta/m/v %.0f MB per step" % (
                        n * B * s_bytes / 1e6, n * B * 12 / 1e6),
-                   "steps_per_s": 1000.0 * K / total_ms, "tuning": tuning, "best_after_run": best},
+                   "steps_per_s": 1000.0 * K / total_ms, "tuning": tuning,
+                   "plan": {k: info[k] for k in ("fwd_tile_codes", "var_tile_codes", "own_item_codes")},
+                   "tuning_source": tune_rec["source"] if tune_rec else "flags", "best_after_run": best},
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "gpu_launches": launches_per_step * K,
         "legs": legs,
     }

@@ -84,13 +84,15 @@ def library_path() -> str:
 
 
 def lib():
-    """The loaded ``libgaloissat.so`` (raises if it has not been built)."""
+    """The loaded ``libgaloissat.so`` (raises if it has not been built); with the environment
+    variable ``GS_DEBUG=1`` the bounds-checked ``libgaloissat_debug.so`` instead."""
     global _lib
     if _lib is None:
-        path = _build.LIB
+        path = _build.LIB_DEBUG if os.environ.get("GS_DEBUG", "") not in ("", "0") else _build.LIB
         if not os.path.exists(path):
-            raise RuntimeError("libgaloissat.so is not built (run __graft_entry__.build() or "
-                               "python -m paper_2603_28796_b300.build); there is no CPU fallback")
+            raise RuntimeError("%s is not built (run __graft_entry__.build() or "
+                               "python -m paper_2603_28796_b300.build); there is no CPU fallback"
+                               % os.path.basename(path))
         L = ctypes.CDLL(path)
         i32, i64, vp, cp = ctypes.c_int32, ctypes.c_int64, ctypes.c_void_p, ctypes.c_char_p
         pp = ctypes.POINTER(ctypes.c_void_p)

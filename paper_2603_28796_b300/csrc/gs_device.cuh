@@ -71,6 +71,22 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
     return mbar_wait_slow(bar, parity, limit_ns);
 }
 
+// Debug build (GS_DEBUG): a gathered row index must be below n_rows; otherwise the sticky status
+// bit kStatusBounds is set and the caller skips the load. Release builds compile the check away.
+__device__ __forceinline__ bool row_ok(uint64_t u, int64_t n_rows, int32_t* status) {
+#ifdef GS_DEBUG
+    if (u >= static_cast<uint64_t>(n_rows)) {
+        atomicOr(status, kStatusBounds);
+        return false;
+    }
+#else
+    (void)u;
+    (void)n_rows;
+    (void)status;
+#endif
+    return true;
+}
+
 struct Span {
     uintptr_t src;
     uint32_t bytes;   // 16-byte multiple
@@ -132,11 +148,11 @@ int sm_count() {
 }
 
 template <typename K>
-int persistent_grid(K kernel, int smem_bytes) {
+int persistent_grid(K kernel, int smem_bytes, int threads = kThreads) {
     cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
     cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kThreads, smem_bytes) != cudaSuccess ||
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem_bytes) != cudaSuccess ||
         per_sm < 1)
         per_sm = 1;
     return per_sm * sm_count();

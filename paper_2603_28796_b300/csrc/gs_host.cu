@@ -400,6 +400,7 @@ gs_status launch_check_all(gs_problem* p, const uint64_t* bits, int32_t B, int32
     cp.head = p->ctl + kCtlCheckHead;
     cp.exit_cnt = p->ctl + kCtlCheckExit;
     cp.status = p->status;
+    cp.n_rows = p->h.n;
     // at most 32 candidates: gather 32-bit words from a compact copy of the rows' low halves
     const bool words32 = B <= 32 && p->bits32c != nullptr && p->bits32c_cap >= static_cast<size_t>(p->h.n);
     const int64_t total = static_cast<int64_t>(cp.n_items) * cp.n_wchunks;
@@ -507,6 +508,7 @@ gs_status var_pass(gs_problem* p, int mode, const void* x_in, int dtype, int32_t
     vp.head = p->ctl + kCtlVarHead;
     vp.exit_cnt = p->ctl + kCtlVarExit;
     vp.status = p->status;
+    vp.n_rows = p->h.n;
     // lane groups own whole variables (var_split 2) when a chunk leaves more than one group
     const bool own = p->var_split == 2 && c.lc < 32 && p->h.own_ok;
     if (own) {
@@ -899,6 +901,7 @@ gs_status gs_forward(gs_problem* p, const void* x, gs_dtype dtype, int32_t B, in
     fp.head = p->ctl + kCtlFwdHead;
     fp.exit_cnt = p->ctl + kCtlFwdExit;
     fp.status = p->status;
+    fp.n_rows = p->h.n;
     const int64_t total = static_cast<int64_t>(fp.n_items) * c.n_chunks;
     if (total > 0) {
         const int grid = static_cast<int>(std::min<int64_t>(grid_forward(dtype, c.lc), total));
@@ -1048,6 +1051,8 @@ gs_status gs_sync_status(gs_problem* p) {
             return fail(GS_ERR_TIMEOUT, "a bounded device-side wait timed out");
         }
         if (h & kStatusSelect) return fail(GS_ERR_STATE, "a pool selection found more rows than its rank");
+        if (h & kStatusBounds)
+            return fail(GS_ERR_STATE, "a gathered row index was out of range (bounds-checked debug build; load skipped)");
     }
     return GS_OK;
 }
@@ -1148,6 +1153,7 @@ extern "C" gs_status gs_forward_noalloc(gs_problem* p, const void* x, gs_dtype d
     fp.head = head;
     fp.exit_cnt = exit_cnt;
     fp.status = p->status;
+    fp.n_rows = p->h.n;
     GS_CUDA(cudaMemsetAsync(head, 0, 2 * sizeof(int32_t), s), "memset no-alloc counters");
     const int64_t total = static_cast<int64_t>(fp.n_items) * c.n_chunks;
     if (total > 0) {
@@ -1261,6 +1267,7 @@ gs_status gs_st_step(gs_problem* p, float* delta, float* m, float* v, const uint
     sp.head = p->ctl + kCtlVarHead;
     sp.exit_cnt = p->ctl + kCtlVarExit;
     sp.status = p->status;
+    sp.n_rows = p->h.n;
     const int64_t total = static_cast<int64_t>(sp.n_items) * c.n_chunks;
     if (total > 0) {
         const int grid = static_cast<int>(std::min<int64_t>(grid_st_pass(c.lw), total));

@@ -146,6 +146,7 @@ struct VarParams {
     int32_t* head;
     int32_t* exit_cnt;
     int32_t* status;
+    int64_t n_rows;              // variable rows (all instances): the debug build checks gathers against it
 };
 
 // Straight-through Gumbel pass (gs_st_step, Eq. 3-4 with noise): each lane owns one 32-bit word
@@ -181,6 +182,7 @@ struct StParams {
     int32_t* head;
     int32_t* exit_cnt;
     int32_t* status;
+    int64_t n_rows;              // variable rows (all instances): the debug build checks gathers against it
 };
 
 // Candidate pool / branching selection (gs_pool_sample, gs_branch_vars).
@@ -220,6 +222,7 @@ struct FwdParams {
     int32_t* head;
     int32_t* exit_cnt;
     int32_t* status;
+    int64_t n_rows;              // variable rows (all instances): the debug build checks gathers against it
 };
 
 struct CheckParams {
@@ -236,6 +239,7 @@ struct CheckParams {
     int32_t* head;
     int32_t* exit_cnt;
     int32_t* status;
+    int64_t n_rows;              // variable rows (all instances): the debug build checks gathers against it
 };
 
 // Work-queue control words (one int32 array per problem): heads and exit counts of the
@@ -249,6 +253,7 @@ constexpr int kCtlSplit = 8;
 // Device status bits (sticky until read by gs_sync_status).
 constexpr int32_t kStatusTimeout = 1;
 constexpr int32_t kStatusSelect = 2;   // a selection found more rows than its rank (never expected)
+constexpr int32_t kStatusBounds = 4;   // debug build: a gathered row index was out of range (load skipped)
 
 // ---------------------------------------------------------------------------------------------
 // Launchers (gs_kernels.cu). They return cudaGetLastError() of the launch.

@@ -128,7 +128,7 @@ __device__ __forceinline__ void planes_get8(const uint32_t (&P)[kStPlanes], int 
 // candidates for which all of them are false. A unit clause's sentinel code has no literal.
 template <int NB>
 __device__ __forceinline__ void st_occ(const uint32_t* cd, int cs, int ce, const uint32_t* col, int nw32, bool wok,
-                                       uint32_t (&Pl)[kStPlanes]) {
+                                       int64_t n_rows, int32_t* status, uint32_t (&Pl)[kStPlanes]) {
     uint32_t acc = 0u;
     for (int s = cs; s < ce; s += NB) {
         uint32_t cw[NB], wd[NB];
@@ -137,7 +137,8 @@ __device__ __forceinline__ void st_occ(const uint32_t* cd, int cs, int ce, const
 #pragma unroll
         for (int j = 0; j < NB; ++j) {
             const uint32_t u = cw[j] >> kVShift;
-            wd[j] = (wok && u != kVSentinel) ? __ldg(col + static_cast<int64_t>(u) * nw32) : 0u;
+            wd[j] = (wok && u != kVSentinel && row_ok(u, n_rows, status)) ? __ldg(col + static_cast<int64_t>(u) * nw32)
+                                                                             : 0u;
         }
 #pragma unroll
         for (int j = 0; j < NB; ++j) {
@@ -265,7 +266,7 @@ __device__ __forceinline__ void process_st_item(const StParams& P, int w, const 
             uint32_t Pl[kStPlanes];
 #pragma unroll
             for (int k = 0; k < kStPlanes; ++k) Pl[k] = 0u;
-            st_occ<NB>(cd, cs, ce, col, P.nw32, wok, Pl);
+            st_occ<NB>(cd, cs, ce, col, P.nw32, wok, P.n_rows, P.status, Pl);
             reduce_groups<LW>(Pl);
             st_epilogue<LW>(P, v, chunk, lane,
                             [&](int src, int j0, int, float (&gx)[8]) { planes_get8_from(Pl, src, j0, gx); });
@@ -284,7 +285,7 @@ __device__ __forceinline__ void process_st_item(const StParams& P, int w, const 
         uint32_t Pl[kStPlanes];
 #pragma unroll
         for (int k = 0; k < kStPlanes; ++k) Pl[k] = 0u;
-        st_occ<NB>(cd, cs, ce, col, P.nw32, wok, Pl);
+        st_occ<NB>(cd, cs, ce, col, P.nw32, wok, P.n_rows, P.status, Pl);
         reduce_groups<LW>(Pl);
         // this part's integer counts of the lane's 32 candidates
         float* rowp = P.split_part + static_cast<int64_t>(it.split_row + it.part) * P.bpad + word * 32;

@@ -15,11 +15,13 @@ def pytest_configure(config):
 
 @pytest.fixture(scope="session", autouse=True)
 def _native_builds():
-    """Compile the oracle, the input generators and the C-ABI library if they are stale."""
+    """Compile the oracle, the input generators and the C-ABI library (release and bounds-checked
+    debug builds) if they are stale."""
     import oracle
     from paper_2603_28796_b300 import build
 
     oracle.build()
     build.build_synth()
     build.build_library()
+    build.build_library(debug=True)
     yield

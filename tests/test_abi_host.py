@@ -27,6 +27,12 @@ def test_library_loads_and_exports_every_declared_symbol():
     assert set(declared) == set(_abi.EXPORTED)
 
 
+def test_debug_library_exports_the_same_symbols():
+    L = ctypes.CDLL(build.LIB_DEBUG)
+    for name in header_functions():
+        assert hasattr(L, name), name
+
+
 def test_status_strings():
     assert _abi.gs_status_str(0) == "ok"
     assert "timed out" in _abi.gs_status_str(6)
@@ -131,3 +137,43 @@ def test_inspect_statistics_random(seed):
     assert info["n_fwd_tiles"] >= -(-widths.sum() // 512)
     used = np.unique(np.abs(lits))
     assert info["n_var_tiles"] >= -(-len(used) // 64)
+
+
+def test_load_with_tile_caps_out_of_range_is_refused_on_the_host():
+    cnf = synth.planted_ksat(100, 400, 3, seed=4)
+    for bad in (dict(fwd_tile_codes=16), dict(fwd_tile_codes=1024), dict(var_tile_codes=400),
+                dict(own_item_codes=100), dict(own_item_codes=70000)):
+        with pytest.raises(_abi.GSError) as ei:
+            _abi.gs_load_batch_opts([cnf.n_vars], [cnf.n_clauses], cnf.clause_ptr, cnf.lits, stream=0, **bad)
+        assert ei.value.status == 1 and "tile caps" in str(ei.value)
+
+
+def test_inspect_reports_default_tile_caps():
+    cnf = synth.planted_ksat(100, 400, 3, seed=4)
+    info = _abi.gs_inspect_cnf(cnf.n_vars, cnf.clause_ptr, cnf.lits)
+    assert (info["fwd_tile_codes"], info["var_tile_codes"], info["own_item_codes"]) == (512, 384, 4096)
+
+
+def test_tuning_cache_key_and_round_trip(tmp_path, monkeypatch):
+    from paper_2603_28796_b300 import tuning
+
+    a = synth.planted_ksat(300, 1200, 3, seed=1)
+    b = synth.planted_ksat(300, 1200, 4, seed=1)       # same sizes, other clause widths
+    sa = tuning.signature(a, 64, "f32", device="dev0")
+    sb = tuning.signature(b, 64, "f32", device="dev0")
+    assert sa["n"] == 300 and sa["m"] == 1200 and sa["nnz"] == 3600 and sa["n_inst"] == 1
+    assert sa["khist"] != sb["khist"]
+    assert tuning.signature(a, 128, "f32", device="dev0") != sa
+    batch = synth.concat([a, b])
+    sc = tuning.signature(batch, 64, "f32", device="dev0")
+    assert sc["n_inst"] == 2 and sc["n"] == 600 and sc["nnz"] == 3600 + 4800
+    path = str(tmp_path / "cache.json")
+    monkeypatch.setenv("GS_TUNING_CACHE", path)
+    assert tuning.lookup(sa) is None
+    entry = {"plan": {"fwd_tile_codes": 256, "var_tile_codes": 192, "own_item_codes": 2048},
+             "tuning": {"var_lanes": 16, "fwd_lanes": 32, "var_gather": 1, "loss_mode": 1, "var_split": 2},
+             "ms_per_step": 1.0}
+    tuning.save_entry(sa, entry)
+    hit = tuning.lookup(sa)
+    assert hit["plan"] == entry["plan"] and hit["tuning"] == entry["tuning"] and hit["key"] == sa
+    assert tuning.lookup(sb) is None

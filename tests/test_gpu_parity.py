@@ -515,3 +515,47 @@ def test_allocation_failure_is_reported():
         H.assert_loss(loss.cpu().numpy()[0], lu)
     finally:
         prob.close()
+
+
+@pytest.mark.parametrize("caps", [dict(fwd_tile_codes=32, var_tile_codes=32, own_item_codes=256),
+                                  dict(fwd_tile_codes=256, var_tile_codes=192, own_item_codes=2048),
+                                  dict(fwd_tile_codes=512, var_tile_codes=384, own_item_codes=65536)])
+@pytest.mark.parametrize("name", ["3sat", "mixed", "edge", "community"])
+def test_tile_caps(name, caps):
+    """Tile sizes chosen at load time (gs_plan_opts): small caps make many tiles and split every
+    variable with more than 32 codes; forward, backward, the fused step in both variable-pass
+    forms and the check keep their parity with the oracle."""
+    cnf = CNFS[name]()
+    prob = _abi.gs_load_batch_opts([cnf.n_vars], [cnf.n_clauses], cnf.clause_ptr, cnf.lits, **caps)
+    info = prob.info()
+    assert (info["fwd_tile_codes"], info["var_tile_codes"], info["own_item_codes"]) == (
+        caps["fwd_tile_codes"], caps["var_tile_codes"], caps["own_item_codes"])
+    n = cnf.n_vars
+    for B, dtype, tuning in ((200, "f32", {}), (40, "bf16", dict(var_lanes=4, var_split=2))):
+        _abi.gs_set_tuning(prob, **tuning)
+        x = H.device_cands(synth.uniform_values(n, B, seed=41), B, dtype)
+        xh = H.host64(x)
+        loss = _abi.gs_forward(prob, x)
+        grad = _abi.gs_backward(prob, x)
+        d0 = synth.init_delta(n, B, seed=42)
+        delta = H.device_cands(d0, B)
+        m, v = H.device_cands(np.zeros((n, B), np.float32), B), H.device_cands(np.zeros((n, B), np.float32), B)
+        xout = candidates(n, B, H.TORCH_DT[dtype])
+        lstep = torch.zeros((1, B), dtype=torch.float64, device="cuda")
+        bits = torch.zeros((n, (B + 63) // 64), dtype=torch.int64, device="cuda")
+        _abi.gs_step(prob, delta, m, v, 1, x_in=x, x_out=xout, loss=lstep, bits=bits)
+        unsat, best = _abi.gs_check_bits(prob, bits, B)
+        torch.cuda.synchronize()
+        lu, _ = oracle.forward(n, cnf.clause_ptr, cnf.lits, xh)
+        g_ref, scale = oracle.backward(n, cnf.clause_ptr, cnf.lits, xh)
+        H.assert_loss(loss.cpu().numpy()[0], lu, "forward")
+        H.assert_loss(lstep.cpu().numpy()[0], lu, "fused loss")
+        H.assert_grad(H.host64(grad), g_ref, scale)
+        d_ref, m_ref, v_ref, _ = oracle.adam(d0[:, :B], np.zeros((n, B)), np.zeros((n, B)), g_ref, 1)
+        tol = H.adam_tolerances(d0[:, :B], np.zeros((n, B)), np.zeros((n, B)), g_ref, scale, 1)
+        dg = H.host64(delta)
+        H.check_adam(dict(delta=dg, m=H.host64(m), v=H.host64(v)), dict(delta=d_ref, m=m_ref, v=v_ref), tol, name)
+        _, u_ref, b_ref = oracle.round_check(n, cnf.clause_ptr, cnf.lits, dg)
+        assert np.array_equal(unsat.cpu().numpy()[0], u_ref) and int(best.cpu().numpy()[0]) == b_ref
+    _abi.gs_sync_status(prob)
+    prob.close()
