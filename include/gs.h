@@ -432,7 +432,7 @@ gs_status gs_branch_vars(gs_problem* prob, const float* delta, int64_t stride, i
  * gs_gather_probe - measurement kernel for the roofline of the variable-major pass (the K7 probe
  * of the measurement plan; no counterpart in the paper): n_gathers random row reads of row_bytes
  * bytes each, 16 bytes per lane, row_bytes / 16 lanes per row, 8 reads in flight per lane, with
- * the same L2 eviction hint as the pass's gathers. Row k is at src + idx[k] * row_stride; an
+ * the load form of the pass's gathers (16-byte non-coherent loads). Row k is at src + idx[k] * row_stride; an
  * index >= n_rows is skipped (no read). The loaded words are folded into *sink (XOR, one atomic
  * per warp) so that the reads are not removed. Time it with events to get the random-row gather
  * rate of the memory hierarchy at that row size and working set (n_rows x row_bytes).

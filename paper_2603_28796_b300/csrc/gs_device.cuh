@@ -1,6 +1,6 @@
 // Device helpers shared by the kernel translation units (gs_kernels.cu, gs_st.cu): mbarrier
-// and 1-D bulk-copy PTX wrappers with bounded waits, the integer work queue, L2 cache-policy
-// hints, and the persistent-grid sizing of the tiled kernels. Internal linkage in each unit.
+// and 1-D bulk-copy PTX wrappers with bounded waits, the integer work queue, the debug-build row
+// check, and the persistent-grid sizing of the tiled kernels. Internal linkage in each unit.
 #pragma once
 #include <cuda.h>
 #include <cuda_runtime.h>
@@ -122,18 +122,6 @@ __device__ __forceinline__ int fetch_work(int32_t* head, int lane) {
     return __shfl_sync(0xffffffffu, w, 0);
 }
 
-// L2 eviction policies: the gathered relaxed values of the current candidate chunk should stay
-// in L2 (evict_last) while the once-per-step state streams pass through it (evict_first).
-__device__ __forceinline__ uint64_t l2_evict_last() {
-    uint64_t p;
-    asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
-    return p;
-}
-__device__ __forceinline__ uint64_t l2_evict_first() {
-    uint64_t p;
-    asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
-    return p;
-}
 // ------------------------------------------------------------------------------------------
 // Host side: persistent grids (SMs x resident CTAs at the kernel's shared-memory footprint).
 int sm_count() {

@@ -13,11 +13,10 @@ namespace {
 
 constexpr int kProbeBatch = 8;   // gathers in flight per lane group, as in the variable pass
 
-__device__ __forceinline__ uint4 probe_ld16(const void* p, uint64_t pol) {
+// The load form of the variable pass's gathers: 16-byte non-coherent loads, no L2 policy.
+__device__ __forceinline__ uint4 probe_ld16(const void* p) {
     uint4 r;
-    asm volatile("ld.global.nc.L2::cache_hint.v4.u32 {%0, %1, %2, %3}, [%4], %5;"
-                 : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w)
-                 : "l"(p), "l"(pol));
+    asm volatile("ld.global.nc.v4.u32 {%0, %1, %2, %3}, [%4];" : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w) : "l"(p));
     return r;
 }
 
@@ -33,7 +32,6 @@ __global__ void __launch_bounds__(kThreads) k_gather_probe(const char* src, int6
     const int g = lane / LPR, li = lane % LPR;
     const int64_t groups_total = static_cast<int64_t>(gridDim.x) * (blockDim.x / 32) * G;
     const int64_t gid = (static_cast<int64_t>(blockIdx.x) * (blockDim.x / 32) + (threadIdx.x >> 5)) * G + g;
-    const uint64_t pol = l2_evict_last();
     uint32_t acc = 0;
     for (int64_t base = gid * kProbeBatch; base < n; base += groups_total * kProbeBatch) {
         uint32_t r[kProbeBatch];
@@ -43,7 +41,7 @@ __global__ void __launch_bounds__(kThreads) k_gather_probe(const char* src, int6
 #pragma unroll
         for (int j = 0; j < kProbeBatch; ++j) {
             v[j] = make_uint4(0u, 0u, 0u, 0u);
-            if (r[j] < n_rows) v[j] = probe_ld16(src + static_cast<int64_t>(r[j]) * stride + li * 16, pol);
+            if (r[j] < n_rows) v[j] = probe_ld16(src + static_cast<int64_t>(r[j]) * stride + li * 16);
         }
 #pragma unroll
         for (int j = 0; j < kProbeBatch; ++j) acc ^= v[j].x ^ v[j].y ^ v[j].z ^ v[j].w;

@@ -33,43 +33,42 @@ struct Elem<__half> {
     static constexpr int VEC = 8;
 };
 
+// One 16-byte piece of a relaxed-value row, through the non-coherent path. No L2 policy
+// operand: each one costs the pass an instruction per gather (an explicit evict-last policy on
+// the gathers measured 4-10 % slower across the workloads).
 __device__ __forceinline__ uint4 ld_gather16(const void* p) {
     uint4 r;
-    asm("ld.global.nc.L2::cache_hint.v4.u32 {%0, %1, %2, %3}, [%4], %5;"
+    asm("ld.global.nc.v4.u32 {%0, %1, %2, %3}, [%4];"
         : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w)
-        : "l"(p), "l"(l2_evict_last()));
+        : "l"(p));
     return r;
 }
+// Once-per-step state streams (delta, m, v read; delta, m, v, x_out written): the streaming cache
+// operator (.cs, evict-first in L1 and L2) keeps them from displacing the gathered rows.
 __device__ __forceinline__ float4 ld_first_f4(const float* p) {
     float4 r;
-    asm volatile("ld.global.L1::no_allocate.L2::cache_hint.v4.f32 {%0, %1, %2, %3}, [%4], %5;"
-                 : "=f"(r.x), "=f"(r.y), "=f"(r.z), "=f"(r.w)
-                 : "l"(p), "l"(l2_evict_first()));
+    asm volatile("ld.global.cs.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(r.x), "=f"(r.y), "=f"(r.z), "=f"(r.w) : "l"(p));
     return r;
 }
 __device__ __forceinline__ float2 ld_first_f2(const float* p) {
     float2 r;
-    asm volatile("ld.global.L1::no_allocate.L2::cache_hint.v2.f32 {%0, %1}, [%2], %3;"
-                 : "=f"(r.x), "=f"(r.y)
-                 : "l"(p), "l"(l2_evict_first()));
+    asm volatile("ld.global.cs.v2.f32 {%0, %1}, [%2];" : "=f"(r.x), "=f"(r.y) : "l"(p));
     return r;
 }
 __device__ __forceinline__ float ld_first_f1(const float* p) {
     float r;
-    asm volatile("ld.global.L1::no_allocate.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(r) : "l"(p), "l"(l2_evict_first()));
+    asm volatile("ld.global.cs.f32 %0, [%1];" : "=f"(r) : "l"(p));
     return r;
 }
 __device__ __forceinline__ void st_first_u4(void* p, uint4 v) {
-    asm volatile("st.global.L2::cache_hint.v4.u32 [%0], {%1, %2, %3, %4}, %5;" ::"l"(p), "r"(v.x), "r"(v.y), "r"(v.z),
-                 "r"(v.w), "l"(l2_evict_first())
+    asm volatile("st.global.cs.v4.u32 [%0], {%1, %2, %3, %4};" ::"l"(p), "r"(v.x), "r"(v.y), "r"(v.z), "r"(v.w)
                  : "memory");
 }
 __device__ __forceinline__ void st_first_u2(void* p, uint2 v) {
-    asm volatile("st.global.L2::cache_hint.v2.u32 [%0], {%1, %2}, %3;" ::"l"(p), "r"(v.x), "r"(v.y), "l"(l2_evict_first())
-                 : "memory");
+    asm volatile("st.global.cs.v2.u32 [%0], {%1, %2};" ::"l"(p), "r"(v.x), "r"(v.y) : "memory");
 }
 __device__ __forceinline__ void st_first_u1(void* p, uint32_t v) {
-    asm volatile("st.global.L2::cache_hint.u32 [%0], %1, %2;" ::"l"(p), "r"(v), "l"(l2_evict_first()) : "memory");
+    asm volatile("st.global.cs.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
 template <typename T>
@@ -229,11 +228,26 @@ __device__ __forceinline__ void kahan_add(float& s, float& c, float x) {
     s = t;
 }
 
+// Hardware approximations for the Adam epilogue: rcp.approx.f32 (at most 1 ulp from the
+// reciprocal) and sqrt.approx.f32 (relative error at most 2^-23). The update's error bound in the
+// tests allows a few float32 roundings per operation; the IEEE-rounded forms cost several
+// instructions each and the pass is bound by instruction issue.
+__device__ __forceinline__ float rcp_fast(float x) {
+    float r;
+    asm("rcp.approx.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ float sqrt_fast(float x) {
+    float r;
+    asm("sqrt.approx.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
 // Logistic sigmoid, overflow-free: with e = exp(-|z|), sigma(|z|) = 1 / (1 + e) and
 // sigma(-|z|) = e / (1 + e).
 __device__ __forceinline__ float sigmoid(float z) {
     const float e = expf(-fabsf(z));
-    const float r = __frcp_rn(1.0f + e);
+    const float r = rcp_fast(1.0f + e);
     return z >= 0.0f ? r : e * r;
 }
 
@@ -242,13 +256,13 @@ __device__ __forceinline__ float sigmoid(float z) {
 __device__ __forceinline__ void adam_update(float gx, float& d, float& m, float& v, float& x_new, const AdamK& k) {
     const float z = d * k.inv_tau;
     const float e = expf(-fabsf(z));
-    const float r = __frcp_rn(1.0f + e);
+    const float r = rcp_fast(1.0f + e);
     const float q = e * r;
     const float g = gx * (r * q) * k.inv_tau;
     m = fmaf(k.beta1, m, k.one_minus_beta1 * g);
     v = fmaf(k.beta2, v, k.one_minus_beta2 * (g * g));
-    const float den = sqrtf(v) * k.inv_sqrt_bc2 + k.eps;
-    d = d - k.step_size * (m * __frcp_rn(den));
+    const float den = sqrt_fast(v) * k.inv_sqrt_bc2 + k.eps;
+    d = d - k.step_size * (m * rcp_fast(den));
     x_new = sigmoid(d * k.inv_tau);
 }
 
@@ -330,9 +344,11 @@ struct Credits {
 // General slot loop over the occurrence codes [cs, ce) of the group, NB codes per batch; an
 // occurrence ends at a code carrying kVEnd. R is the running leave-one-out product (prefix then
 // suffix of the occurrence's clause), restarted after each end.
-template <typename T, int VEC, int NB, bool LOSS, bool GC>
-__device__ __forceinline__ void var_slots(const uint32_t* cd, int cs, int ce, const RowView& rv, float2 (&G2)[VEC / 2],
-                                          Credits<VEC / 2>& cr) {
+// UNI: all 32 lanes of the warp process the same codes (one lane group), so branches on a code's
+// flags are uniform and the loss credit is added only where a code carries it.
+template <typename T, int VEC, int NB, bool LOSS, bool GC, bool UNI = false>
+__device__ __forceinline__ void var_slots(const uint32_t* cd, int cs, int ce, const RowView& rv,
+                                          float2 (&G2)[VEC / 2], Credits<VEC / 2>& cr) {
     constexpr int H = VEC / 2;
     float2 R[H];
 #pragma unroll
@@ -359,24 +375,53 @@ __device__ __forceinline__ void var_slots(const uint32_t* cd, int cs, int ce, co
             float2 f[H];
             factors<T>(raw[j], a, b, f);
             const bool end = (c & kVEnd) != 0u;
-            const float sg = end ? occ_sign(c) : 0.0f;
-            const float e1 = end ? 1.0f : 0.0f;   // restart the running product after an end:
-            const float keep = 1.0f - e1;         // R = rn * keep + e1 (rn is finite)
             float2 rn[H];
+            if constexpr (UNI) {
+                // one lane group: the end of an occurrence is a uniform branch
 #pragma unroll
-            for (int h = 0; h < H; ++h) {
-                rn[h] = __fmul2_rn(R[h], f[h]);
-                G2[h] = __ffma2_rn(dup2(sg), rn[h], G2[h]);
-                R[h] = __ffma2_rn(rn[h], dup2(keep), dup2(e1));
-            }
-            if (LOSS) {
-                const uint32_t f = c & (kVEnd | kVCredit | kVSelfNeg);
-                const float wp = (f == (kVEnd | kVCredit)) ? 1.0f : 0.0f;
-                const float wn = (f == (kVEnd | kVCredit | kVSelfNeg)) ? 1.0f : 0.0f;
+                for (int h = 0; h < H; ++h) rn[h] = __fmul2_rn(R[h], f[h]);
+                if (end) {
+                    const float sg = occ_sign(c);
+#pragma unroll
+                    for (int h = 0; h < H; ++h) {
+                        G2[h] = __ffma2_rn(dup2(sg), rn[h], G2[h]);
+                        R[h] = dup2(1.0f);
+                    }
+                } else {
+#pragma unroll
+                    for (int h = 0; h < H; ++h) R[h] = rn[h];
+                }
+            } else {
+                const float sg = end ? occ_sign(c) : 0.0f;
+                const float e1 = end ? 1.0f : 0.0f;   // restart the running product after an end:
+                const float keep = 1.0f - e1;         // R = rn * keep + e1 (rn is finite)
 #pragma unroll
                 for (int h = 0; h < H; ++h) {
-                    cr.p[h] = __ffma2_rn(dup2(wp), rn[h], cr.p[h]);
-                    cr.n[h] = __ffma2_rn(dup2(wn), rn[h], cr.n[h]);
+                    rn[h] = __fmul2_rn(R[h], f[h]);
+                    G2[h] = __ffma2_rn(dup2(sg), rn[h], G2[h]);
+                    R[h] = __ffma2_rn(rn[h], dup2(keep), dup2(e1));
+                }
+            }
+            if (LOSS) {
+                if constexpr (UNI) {
+                    if (c & kVCredit) {
+                        if (c & kVSelfNeg) {
+#pragma unroll
+                            for (int h = 0; h < H; ++h) cr.n[h] = __ffma2_rn(dup2(1.0f), rn[h], cr.n[h]);
+                        } else {
+#pragma unroll
+                            for (int h = 0; h < H; ++h) cr.p[h] = __ffma2_rn(dup2(1.0f), rn[h], cr.p[h]);
+                        }
+                    }
+                } else {
+                    const uint32_t f = c & (kVEnd | kVCredit | kVSelfNeg);
+                    const float wp = (f == (kVEnd | kVCredit)) ? 1.0f : 0.0f;
+                    const float wn = (f == (kVEnd | kVCredit | kVSelfNeg)) ? 1.0f : 0.0f;
+#pragma unroll
+                    for (int h = 0; h < H; ++h) {
+                        cr.p[h] = __ffma2_rn(dup2(wp), rn[h], cr.p[h]);
+                        cr.n[h] = __ffma2_rn(dup2(wn), rn[h], cr.n[h]);
+                    }
                 }
             }
         }
@@ -397,9 +442,9 @@ __device__ __forceinline__ void fixed_ab(uint32_t c, float& a, float& b) {
     }
 }
 
-template <typename T, int VEC, int K, int OB, bool LOSS, bool TAIL, bool GC>
-__device__ __forceinline__ void occ_batch(const uint32_t* cd, int s, int ce, const RowView& rv, float2 (&G2)[VEC / 2],
-                                          Credits<VEC / 2>& cr) {
+template <typename T, int VEC, int K, int OB, bool LOSS, bool TAIL, bool GC, bool UNI = false>
+__device__ __forceinline__ void occ_batch(const uint32_t* cd, int s, int ce, const RowView& rv,
+                                          float2 (&G2)[VEC / 2], Credits<VEC / 2>& cr) {
     constexpr int H = VEC / 2;
     constexpr int NS = OB * K;
     uint32_t cw[NS];
@@ -427,6 +472,23 @@ __device__ __forceinline__ void occ_batch(const uint32_t* cd, int s, int ce, con
         }
         const uint32_t last = cw[o * K + K - 1];
         const bool valid = !TAIL || (s + o * K) < ce;
+        if constexpr (UNI) {
+            if (valid) {
+                const float sg = (last & kVSelfNeg) ? 1.0f : -1.0f;
+#pragma unroll
+                for (int h = 0; h < H; ++h) G2[h] = __ffma2_rn(dup2(sg), prod[h], G2[h]);
+                if (LOSS && (last & kVCredit)) {
+                    if (last & kVSelfNeg) {
+#pragma unroll
+                        for (int h = 0; h < H; ++h) cr.n[h] = __ffma2_rn(dup2(1.0f), prod[h], cr.n[h]);
+                    } else {
+#pragma unroll
+                        for (int h = 0; h < H; ++h) cr.p[h] = __ffma2_rn(dup2(1.0f), prod[h], cr.p[h]);
+                    }
+                }
+            }
+            continue;
+        }
         const float sg = valid ? occ_sign(last) : 0.0f;
 #pragma unroll
         for (int h = 0; h < H; ++h) G2[h] = __ffma2_rn(dup2(sg), prod[h], G2[h]);
@@ -443,19 +505,19 @@ __device__ __forceinline__ void occ_batch(const uint32_t* cd, int s, int ce, con
     }
 }
 
-template <typename T, int VEC, int K, bool LOSS, bool GC>
+template <typename T, int VEC, int K, bool LOSS, bool GC, bool UNI = false>
 __device__ __forceinline__ void var_occ_fixed(const uint32_t* cd, int cs, int ce, const RowView& rv,
                                               float2 (&G2)[VEC / 2], Credits<VEC / 2>& cr) {
     constexpr int OB = (K == 1) ? 8 : (K == 2 ? 4 : 3);
     constexpr int NS = OB * K;
     int s = cs;
-    for (; s + NS <= ce; s += NS) occ_batch<T, VEC, K, OB, LOSS, false, GC>(cd, s, ce, rv, G2, cr);
-    if (s < ce) occ_batch<T, VEC, K, OB, LOSS, true, GC>(cd, s, ce, rv, G2, cr);
+    for (; s + NS <= ce; s += NS) occ_batch<T, VEC, K, OB, LOSS, false, GC, UNI>(cd, s, ce, rv, G2, cr);
+    if (s < ce) occ_batch<T, VEC, K, OB, LOSS, true, GC, UNI>(cd, s, ce, rv, G2, cr);
 }
 
 // Gradient and (with LOSS) loss credits of one variable's occurrence codes [cs, ce); GC: the
 // codes are read from global memory instead of a shared-memory tile.
-template <typename T, int VEC, int NB, bool LOSS, bool GC = false>
+template <typename T, int VEC, int NB, bool LOSS, bool GC = false, bool UNI = false>
 __device__ __forceinline__ void var_gather(int kk, const uint32_t* cd, int cs, int ce, const RowView& rv,
                                            float (&gacc)[VEC], Credits<VEC / 2>& cr) {
     constexpr int H = VEC / 2;
@@ -463,10 +525,10 @@ __device__ __forceinline__ void var_gather(int kk, const uint32_t* cd, int cs, i
 #pragma unroll
     for (int h = 0; h < H; ++h) G2[h] = dup2(0.0f);
     switch (kk) {
-        case 1: var_occ_fixed<T, VEC, 1, LOSS, GC>(cd, cs, ce, rv, G2, cr); break;
-        case 2: var_occ_fixed<T, VEC, 2, LOSS, GC>(cd, cs, ce, rv, G2, cr); break;
-        case 3: var_occ_fixed<T, VEC, 3, LOSS, GC>(cd, cs, ce, rv, G2, cr); break;
-        default: var_slots<T, VEC, NB, LOSS, GC>(cd, cs, ce, rv, G2, cr); break;
+        case 1: var_occ_fixed<T, VEC, 1, LOSS, GC, UNI>(cd, cs, ce, rv, G2, cr); break;
+        case 2: var_occ_fixed<T, VEC, 2, LOSS, GC, UNI>(cd, cs, ce, rv, G2, cr); break;
+        case 3: var_occ_fixed<T, VEC, 3, LOSS, GC, UNI>(cd, cs, ce, rv, G2, cr); break;
+        default: var_slots<T, VEC, NB, LOSS, GC, UNI>(cd, cs, ce, rv, G2, cr); break;
     }
 #pragma unroll
     for (int h = 0; h < H; ++h) {
