@@ -206,6 +206,8 @@ def cpu_oracle_sample(cnf, B_sample, seed, target_s, max_steps=None):
     import oracle
     from paper_2603_28796_b300 import synth
 
+    if hasattr(cnf, "n_inst"):       # a batch: the oracle runs its first instance
+        cnf = cnf.instance(0)
     n = cnf.n_vars
     d = synth.init_delta(n, B_sample, seed).astype(np.float64)
     m = np.zeros_like(d)
@@ -594,6 +596,9 @@ def run_reference(args):
     if rank != 0:
         return 0
     cnf, B, dtype, desc = workload_setup(args.workload, args.dtype, args.scale)
+    if hasattr(cnf, "n_inst"):       # a batch: the oracle runs its first instance
+        desc += "; oracle sample: instance 0"
+        cnf = cnf.instance(0)
     B_sample = 16
     import oracle
 
@@ -632,11 +637,28 @@ def run_native(args):
     torch.cuda.set_device(dev)
 
     cnf, B, dtype, desc = workload_setup(args.workload, args.dtype, args.scale)
+    full = cnf
+    inst_ids = None
+    if hasattr(cnf, "n_inst"):
+        # a batch of instances: under torchrun each rank takes a share of whole instances,
+        # balanced by literal count (the job's total work is fixed: strong scaling)
+        if world > 1:
+            c_off = np.concatenate([[0], np.cumsum(cnf.n_clauses)]).astype(np.int64)
+            inst_nnz = np.diff(cnf.clause_ptr[c_off])
+            inst_ids = shard.partition_instances(inst_nnz, world)[rank]
+            nv, nc, cp, lt = shard.sub_batch(cnf.n_vars, cnf.n_clauses, cnf.clause_ptr, cnf.lits, inst_ids)
+            cnf = synth.Batch(nv, nc, cp, lt, np.zeros(int(nv.sum()), np.uint8), cnf.name)
+        n, nnz, m = int(np.sum(cnf.n_vars)), int(cnf.clause_ptr[-1]), int(np.sum(cnf.n_clauses))
+    else:
+        n, nnz, m = cnf.n_vars, cnf.nnz, cnf.n_clauses
     if args.scale != 1.0:
-        desc += " (formula scaled by %g: n=%d, m=%d)" % (args.scale, cnf.n_vars, cnf.n_clauses)
+        desc += " (formula scaled by %g: n=%d, m=%d)" % (args.scale, n, m)
     tune_rec = None
     if args.var_lanes or args.var_gather or args.var_split or args.loss_mode or args.no_autotune:
-        prob = _abi.gs_load_cnf(cnf.n_vars, cnf.clause_ptr, cnf.lits)
+        if hasattr(cnf, "n_inst"):
+            prob = _abi.gs_load_batch(cnf.n_vars, cnf.n_clauses, cnf.clause_ptr, cnf.lits)
+        else:
+            prob = _abi.gs_load_cnf(cnf.n_vars, cnf.clause_ptr, cnf.lits)
         _abi.gs_set_tuning(prob, var_lanes=args.var_lanes, var_gather=args.var_gather, var_split=args.var_split,
                            loss_mode=args.loss_mode)
     else:
@@ -644,7 +666,6 @@ def run_native(args):
     tuning = _abi.gs_get_tuning(prob)
     info = prob.info()
     eng = Engine(prob, B, dtype, seed=shard.rank_seed(1, rank))
-    nnz, n = cnf.nnz, cnf.n_vars
     evals_per_step = nnz * B
     s_bytes = {"f32": 4, "bf16": 2, "f16": 2}[dtype]
 
@@ -684,10 +705,23 @@ def run_native(args):
     _abi.gs_sync_status(prob)
     # the run's one cross-rank exchange (outside the timed region): the best candidate over all
     # ranks and its rounded assignment
-    b_rank, b_cand, b_unsat, _ = shard.global_best(eng.unsat, eng.best, eng.bits, n=cnf.n_vars)
-    best = {"unsat": b_unsat, "rank": b_rank, "candidate": b_cand, "of": B * world}
+    if hasattr(full, "n_inst"):
+        table = shard.global_best_instances(inst_ids if inst_ids is not None else range(prob.n_inst), eng.unsat,
+                                            eng.best, full.n_inst)
+        best = {"instances": int(full.n_inst), "solved_instances": int((table[:, 0] == 0).sum()),
+                "sum_of_best_unsat": int(table[:, 0].clamp(min=0).sum())}
+    else:
+        b_rank, b_cand, b_unsat, _ = shard.global_best(eng.unsat, eng.best, eng.bits, n=n)
+        best = {"unsat": b_unsat, "rank": b_rank, "candidate": b_cand, "of": B * world}
 
-    value = evals_per_step * K * world / (total_ms / 1000.0)
+    # evals of the whole job: every rank's literals x candidates (ranks hold equal formulas under
+    # the candidate split, shares of the batch under the instance split)
+    job_evals = evals_per_step * world
+    if world > 1 and inst_ids is not None:
+        t = torch.tensor([float(evals_per_step)], dtype=torch.float64, device=dev)
+        dist.all_reduce(t)
+        job_evals = float(t.item())
+    value = job_evals * K / (total_ms / 1000.0)
     # launches per step: the variable pass and its two loss-reduction kernels, the check and its
     # two count-reduction kernels (+ the bit-row compaction for B <= 32, + the forward pass and
     # its two reduction kernels when the loss comes from a separate pass)
@@ -808,10 +842,12 @@ def run_native(args):
 
     line = {
         "metric": "fwd+bwd clause-literal evals/s", "value": value, "unit": "evals/s", "n_gpus": world, "steps": K,
-        "warmup": max(3, args.warmup), "ms_per_step": total_ms / K, "higher_is_better": True, "scaling": "weak",
+        "warmup": max(3, args.warmup), "ms_per_step": total_ms / K, "higher_is_better": True,
+        "scaling": "strong" if inst_ids is not None else "weak",
         "vs_baseline": None, "dtype": dtype, "data": "synthetic",
-        "config": {"workload": desc, "n": n, "m": cnf.n_clauses, "nnz": nnz, "B": B, "global_batch": B * world,
-                   "parallelism": "dp%d (independent candidate batches)" % world,
+        "config": {"workload": desc, "n": n, "m": m, "nnz": nnz, "B": B, "global_batch": B * world,
+                   "parallelism": ("dp%d (instances split over ranks by literal count)" % world) if inst_ids is not None
+                   else "dp%d (independent candidate batches)" % world,
                    "l2": "inputs larger than L2: x %.0f MB + delta/m/v %.0f MB per step" % (
                        n * B * s_bytes / 1e6, n * B * 12 / 1e6),
                    "steps_per_s": 1000.0 * K / total_ms, "tuning": tuning,
