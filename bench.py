@@ -269,6 +269,14 @@ def _gather_model_bytes(nnz, n, B, s):
     return nnz * B * 2 * s + n * B * (24 + s)
 
 
+def _row_read_stats(prob, B, s, step_ms):
+    """Actual row reads of one variable pass: every occurrence code (one other literal of one
+    occurrence, sum over clauses of k(k-1)) reads one candidate row slice of B*s bytes, which
+    for clauses wider than 3 is more than the gather model's two reads per literal."""
+    rr = prob.info()["n_occ_codes"] * B * s
+    return {"row_read_bytes": rr, "row_read_GBps": rr / (step_ms / 1000.0) / 1e9}
+
+
 def _compulsory_bytes(n, B, s):
     """Strict DRAM floor of one fused step: delta, m, v read and written, x read once and
     written once, the bit rows written (index data excluded)."""
@@ -294,7 +302,8 @@ def leg_precision(torch, args, peak):
         out[dtype] = {"ms_per_step": ms, "steps_per_s": 1000.0 / ms, "evals_per_s": nnz * B / (ms / 1000.0),
                       "gs_step_ms": step_ms, "gather_model_GBps": gm / (step_ms / 1000.0) / 1e9,
                       "gather_model_frac": gm / (step_ms / 1000.0) / 1e9 / peak,
-                      "compulsory_frac": cb / (step_ms / 1000.0) / 1e9 / peak, "tuning": tuning}
+                      "compulsory_frac": cb / (step_ms / 1000.0) / 1e9 / peak, "tuning": tuning,
+                      **_row_read_stats(prob, B, s, step_ms)}
         del eng
         if dtype == "bf16":
             prob.close()
@@ -365,7 +374,8 @@ def leg_structured(torch, args, peak):
            "ms_per_step": ms, "steps_per_s": 1000.0 / ms, "evals_per_s": cnf.nnz * B / (ms / 1000.0),
            "gs_step_ms": step_ms, "gather_model_GBps": gm / (step_ms / 1000.0) / 1e9,
            "gather_model_frac": gm / (step_ms / 1000.0) / 1e9 / peak,
-           "compulsory_frac": cb / (step_ms / 1000.0) / 1e9 / peak, "tuning": tuning}
+           "compulsory_frac": cb / (step_ms / 1000.0) / 1e9 / peak, "tuning": tuning,
+           **_row_read_stats(prob, B, s, step_ms)}
     del eng
     prob.close()
     torch.cuda.empty_cache()
@@ -401,7 +411,8 @@ def leg_batching(torch, args, peak):
     out = {"workload": desc, "n": n, "m": int(sum(batch.n_clauses)), "nnz": nnz, "B": B, "dtype": dtype,
            "batched": {"ms_per_step": ms, "steps_per_s": 1000.0 / ms, "evals_per_s": nnz * B / (ms / 1000.0),
                        "gs_step_ms": step_ms, "gather_model_frac": gm / (step_ms / 1000.0) / 1e9 / peak,
-                       "compulsory_frac": cb / (step_ms / 1000.0) / 1e9 / peak, "tuning": tuning},
+                       "compulsory_frac": cb / (step_ms / 1000.0) / 1e9 / peak, "tuning": tuning,
+                       **_row_read_stats(prob, B, 4, step_ms)},
            "batched_graph": {"ms_per_step": ms_graph, "steps_per_s": 1000.0 / ms_graph,
                              "evals_per_s": nnz * B / (ms_graph / 1000.0), "steps": Kg}}
     # per-instance loop over the same state rows

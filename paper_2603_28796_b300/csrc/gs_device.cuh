@@ -123,7 +123,12 @@ __device__ __forceinline__ int fetch_work(int32_t* head, int lane) {
 }
 
 // ------------------------------------------------------------------------------------------
-// Host side: persistent grids (SMs x resident CTAs at the kernel's shared-memory footprint).
+// Host side: persistent grids (SMs x resident CTAs at the kernel's shared-memory footprint,
+// static and dynamic). The occupancy is found with the whole unified L1/shared array offered as
+// shared memory; the kernel's carve-out is then set to the smallest one that still holds those
+// CTAs, so the rest of the array stays L1 cache for the gathers (a carve-out is a preference: if
+// the smaller one would cost resident CTAs, the maximum is kept). A grid larger than the resident
+// CTAs would leave the surplus waiting for a free slot, so both sides of this must agree.
 int sm_count() {
     static int sms = 0;
     if (!sms) {
@@ -143,6 +148,23 @@ int persistent_grid(K kernel, int smem_bytes, int threads = kThreads) {
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem_bytes) != cudaSuccess ||
         per_sm < 1)
         per_sm = 1;
+    int dev = 0, sm_smem = 0, reserved = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sm_smem, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev);
+    cudaFuncAttributes fa{};
+    const int static_smem = cudaFuncGetAttributes(&fa, kernel) == cudaSuccess ? static_cast<int>(fa.sharedSizeBytes) : 0;
+    if (sm_smem > 0) {
+        const int64_t need = static_cast<int64_t>(per_sm) * (smem_bytes + static_smem + reserved);
+        int pct = static_cast<int>((need * 100 + sm_smem - 1) / sm_smem);
+        pct = pct < 0 ? 0 : (pct > 100 ? 100 : pct);
+        cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
+        int per_sm_l1 = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_l1, kernel, threads, smem_bytes) != cudaSuccess ||
+            per_sm_l1 < per_sm)
+            cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 cudaSharedmemCarveoutMaxShared);
+    }
     return per_sm * sm_count();
 }
 

@@ -17,6 +17,7 @@
 #include <cuda_fp16.h>
 
 #include <cstdint>
+#include <type_traits>
 
 #include "gs_device.cuh"
 #include "gs_internal.h"
@@ -25,34 +26,65 @@
 namespace gs {
 namespace {
 
-// Per-warp shared memory of k_var_pass: two staging buffers and their barriers, then the tile's
-// compensated loss sums (sum and compensation, 32 lanes x VEC candidates each), which live in
-// shared memory rather than registers to leave the registers to the gathers.
-template <typename T>
-__host__ __device__ constexpr int var_warp_bytes() {
-    return kVarWarpBytes + 2 * 32 * Elem<T>::VEC * 4;
+// Where k_var_pass keeps a variable's loss credits. With one lane group per warp a credit is a
+// warp-uniform branch taken on about one code in k, so the sums live in shared memory
+// (CreditsSm) and their 2 * VEC registers go to the gathers: the 16-bit kernel keeps its third
+// resident CTA that way, the float32 one its gathers in flight. Several lane groups credit by
+// predicated arithmetic on every code and keep the sums in registers.
+template <typename T, int LC>
+__host__ __device__ constexpr bool credits_in_smem() {
+    return LC == 32;
 }
 
-// credit_flush on the loss sums in shared memory.
+// Per-warp shared memory of k_var_pass: two staging buffers and their barriers (VarCfg), then the tile's
+// compensated loss sums (sum and compensation, 32 lanes x VEC candidates each), which live in
+// shared memory rather than registers to leave the registers to the gathers, then (see
+// credits_in_smem) the variable's credit sums Cp and Cn (32 lanes x VEC candidates each).
+template <typename T, int LC>
+__host__ __device__ constexpr int var_warp_bytes() {
+    return VarCfg<T, 1, LC>::STAGE_BYTES + 2 * 32 * Elem<T>::VEC * 4 +
+           (credits_in_smem<T, LC>() ? 2 * 32 * Elem<T>::VEC * 4 : 0);
+}
+
+// The tile's compensated loss sums of one lane in shared memory: VEC / 4 16-byte slots of sums
+// then VEC / 4 of compensations, slot q of lane l at q * 512 + l * 16 bytes (conflict-free).
 template <int VEC>
-__device__ __forceinline__ void credit_flush_v(const Credits<VEC / 2>& cr, const float (&xs)[VEC], volatile float* Ls,
-                                               volatile float* Lc) {
-    float s[VEC], c[VEC];
+struct LossSm {
+    uint32_t a;   // shared-memory address of the lane's first slot
+    __device__ __forceinline__ void zero() const {
 #pragma unroll
-    for (int e = 0; e < VEC; ++e) {
-        s[e] = Ls[e];
-        c[e] = Lc[e];
+        for (int q = 0; q < VEC / 2; ++q) st_shared4(a + q * 512, make_float4(0.0f, 0.0f, 0.0f, 0.0f));
     }
+    __device__ __forceinline__ void load(float (&s)[VEC], float (&c)[VEC]) const {
+#pragma unroll
+        for (int q = 0; q < VEC / 4; ++q) {
+            const float4 u = ld_shared4(a + q * 512), v = ld_shared4(a + (VEC / 4 + q) * 512);
+            s[4 * q] = u.x, s[4 * q + 1] = u.y, s[4 * q + 2] = u.z, s[4 * q + 3] = u.w;
+            c[4 * q] = v.x, c[4 * q + 1] = v.y, c[4 * q + 2] = v.z, c[4 * q + 3] = v.w;
+        }
+    }
+    __device__ __forceinline__ void store(const float (&s)[VEC], const float (&c)[VEC]) const {
+#pragma unroll
+        for (int q = 0; q < VEC / 4; ++q) {
+            st_shared4(a + q * 512, make_float4(s[4 * q], s[4 * q + 1], s[4 * q + 2], s[4 * q + 3]));
+            st_shared4(a + (VEC / 4 + q) * 512, make_float4(c[4 * q], c[4 * q + 1], c[4 * q + 2], c[4 * q + 3]));
+        }
+    }
+};
+
+// credit_flush on the loss sums in shared memory.
+template <int VEC, typename CR>
+__device__ __forceinline__ void credit_flush_v(const CR& cr, const float (&xs)[VEC], const LossSm<VEC>& L) {
+    float s[VEC], c[VEC];
+    float2 cp[VEC / 2], cn[VEC / 2];
+    cr.get(cp, cn);
+    L.load(s, c);
 #pragma unroll
     for (int h = 0; h < VEC / 2; ++h) {
-        kahan_add(s[2 * h], c[2 * h], fmaf(1.0f - xs[2 * h], cr.p[h].x, xs[2 * h] * cr.n[h].x));
-        kahan_add(s[2 * h + 1], c[2 * h + 1], fmaf(1.0f - xs[2 * h + 1], cr.p[h].y, xs[2 * h + 1] * cr.n[h].y));
+        kahan_add(s[2 * h], c[2 * h], fmaf(1.0f - xs[2 * h], cp[h].x, xs[2 * h] * cn[h].x));
+        kahan_add(s[2 * h + 1], c[2 * h + 1], fmaf(1.0f - xs[2 * h + 1], cp[h].y, xs[2 * h + 1] * cn[h].y));
     }
-#pragma unroll
-    for (int e = 0; e < VEC; ++e) {
-        Ls[e] = s[e];
-        Lc[e] = c[e];
-    }
+    L.store(s, c);
 }
 
 template <typename T, int MODE, int LC>
@@ -68,7 +100,7 @@ __device__ __forceinline__ void process_var_item(const VarParams& P, int w, cons
     const uint16_t* rc = reinterpret_cast<const uint16_t*>(
         buf + kVarVtabBytes + (reinterpret_cast<uintptr_t>(P.recs + it.rec_base) & 15));
     const uint32_t* cd = reinterpret_cast<const uint32_t*>(
-        buf + kVarVtabBytes + kVarRecBytes + (reinterpret_cast<uintptr_t>(P.codes + it.code_base) & 15));
+        buf + C::CODE_OFF + (reinterpret_cast<uintptr_t>(P.codes + it.code_base) & 15));
     const int cand0 = chunk * C::BC;
     const int lane_base = cand0 + li * VEC;
     const bool ld_ok = lane_base < P.B;
@@ -79,11 +111,14 @@ __device__ __forceinline__ void process_var_item(const VarParams& P, int w, cons
     set_row_bounds(rv, P.n_rows, P.status);
     const bool loss = P.loss_part != nullptr;
     constexpr int H = VEC / 2;
+    using CR = std::conditional_t<credits_in_smem<T, LC>(), CreditsSm<H>, Credits<H>>;
+    CR cr0{};   // zero register sums, or the lane's shared-memory slots
+    if constexpr (credits_in_smem<T, LC>())
+        cr0.a = static_cast<uint32_t>(__cvta_generic_to_shared(lossbuf + 2 * 32 * VEC)) + lane * 16;
 
-    volatile float* Ls = lossbuf + lane * VEC;
-    volatile float* Lc = lossbuf + 32 * VEC + lane * VEC;
-#pragma unroll
-    for (int e = 0; e < VEC; ++e) Ls[e] = Lc[e] = 0.0f;
+    LossSm<VEC> L;
+    L.a = static_cast<uint32_t>(__cvta_generic_to_shared(lossbuf)) + lane * 16;
+    if (loss) L.zero();
 
     if (it.split < 0) {
         for (int vi = 0; vi < it.nv; ++vi) {
@@ -112,9 +147,8 @@ __device__ __forceinline__ void process_var_item(const VarParams& P, int w, cons
                 }
             }
             float gacc[VEC];
-            Credits<H> cr;
-#pragma unroll
-            for (int h = 0; h < H; ++h) cr.p[h] = cr.n[h] = dup2(0.0f);
+            CR cr = cr0;
+            if (credits_in_smem<T, LC>() && loss) cr.zero();
             if (loss) {
                 // the variable's own value (for its loss credits) is requested with the gathers
                 uint4 own_raw = make_uint4(0u, 0u, 0u, 0u);
@@ -122,7 +156,7 @@ __device__ __forceinline__ void process_var_item(const VarParams& P, int w, cons
                 var_gather<T, VEC, C::NB, true, false, (C::G == 1)>(it.kk, cd, cs, ce, rv, gacc, cr);
                 float xs[VEC];
                 unpack<T>(own_raw, xs);
-                credit_flush_v<VEC>(cr, xs, Ls, Lc);
+                credit_flush_v<VEC>(cr, xs, L);
             } else {
                 var_gather<T, VEC, C::NB, false, false, (C::G == 1)>(it.kk, cd, cs, ce, rv, gacc, cr);
             }
@@ -150,16 +184,15 @@ __device__ __forceinline__ void process_var_item(const VarParams& P, int w, cons
             ce = rc[(O * (g + 1)) / G];
         }
         float gacc[VEC];
-        Credits<H> cr;
-#pragma unroll
-        for (int h = 0; h < H; ++h) cr.p[h] = cr.n[h] = dup2(0.0f);
+        CR cr = cr0;
+        if (credits_in_smem<T, LC>() && loss) cr.zero();
         if (loss) {
             var_gather<T, VEC, C::NB, true, false, (C::G == 1)>(it.kk, cd, cs, ce, rv, gacc, cr);
             float xs[VEC];
 #pragma unroll
             for (int e = 0; e < VEC; ++e) xs[e] = 0.0f;
             if (ld_ok) unpack<T>(load_row(rv, static_cast<uint32_t>(v)), xs);
-            credit_flush_v<VEC>(cr, xs, Ls, Lc);
+            credit_flush_v<VEC>(cr, xs, L);
         } else {
             var_gather<T, VEC, C::NB, false, false, (C::G == 1)>(it.kk, cd, cs, ce, rv, gacc, cr);
         }
@@ -195,9 +228,10 @@ __device__ __forceinline__ void process_var_item(const VarParams& P, int w, cons
     }
 
     if (loss) {
-        float lf[VEC];
+        float lf[VEC], lc[VEC];
+        L.load(lf, lc);
 #pragma unroll
-        for (int e = 0; e < VEC; ++e) lf[e] = Ls[e] - Lc[e];
+        for (int e = 0; e < VEC; ++e) lf[e] -= lc[e];
         group_sum<LC>(lf);
         if (g == 0) {
             float* dst = P.loss_part + static_cast<int64_t>(item) * P.bpad + lane_base;
@@ -209,15 +243,18 @@ __device__ __forceinline__ void process_var_item(const VarParams& P, int w, cons
 }
 
 // Register budget: float32 values run 3 CTAs (24 warps) per SM; 16-bit values hold twice the
-// candidates per lane and run 2 CTAs per SM. Shared memory per warp: var_warp_bytes<T>().
+// candidates per lane and run 3 CTAs per SM with one lane group per warp (credits in shared
+// memory), 2 otherwise. Shared memory per warp: var_warp_bytes<T, LC>().
 template <typename T, int MODE, int LC>
-__global__ void __launch_bounds__(kThreads, Elem<T>::VEC == 4 ? 3 : 2) k_var_pass(const VarParams P) {
+__global__ void __launch_bounds__(kThreads, (Elem<T>::VEC == 4 || credits_in_smem<T, LC>()) ? 3 : 2)
+    k_var_pass(const VarParams P) {
     extern __shared__ __align__(128) unsigned char smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int g = lane / LC, li = lane % LC;
-    unsigned char* wbase = smem + warp * var_warp_bytes<T>();
-    uint64_t* bars = reinterpret_cast<uint64_t*>(wbase + 2 * kVarBufBytes);
-    float* lossbuf = reinterpret_cast<float*>(wbase + kVarWarpBytes);
+    unsigned char* wbase = smem + warp * var_warp_bytes<T, LC>();
+    using C = VarCfg<T, MODE, LC>;
+    uint64_t* bars = reinterpret_cast<uint64_t*>(wbase + 2 * C::BUF_BYTES);
+    float* lossbuf = reinterpret_cast<float*>(wbase + C::STAGE_BYTES);
     if (lane == 0) {
         mbar_init(&bars[0], 1);
         mbar_init(&bars[1], 1);
@@ -233,7 +270,7 @@ __global__ void __launch_bounds__(kThreads, Elem<T>::VEC == 4 ? 3 : 2) k_var_pas
         const int wn = fetch_work(P.head, lane);
         if (wn < total && lane == 0) {
             fence_proxy_async();
-            issue_var_item<T, MODE, LC>(P, wn % P.n_items, wbase + (buf ^ 1) * kVarBufBytes, &bars[buf ^ 1]);
+            issue_var_item<T, MODE, LC>(P, wn % P.n_items, wbase + (buf ^ 1) * C::BUF_BYTES, &bars[buf ^ 1]);
         }
         const bool ok = mbar_wait_bounded(&bars[buf], phase[buf], kWaitNs);
         if (!__all_sync(0xffffffffu, ok)) {
@@ -246,7 +283,7 @@ __global__ void __launch_bounds__(kThreads, Elem<T>::VEC == 4 ? 3 : 2) k_var_pas
             break;
         }
         phase[buf] ^= 1u;
-        process_var_item<T, MODE, LC>(P, w, wbase + buf * kVarBufBytes, g, li, lane, lossbuf);
+        process_var_item<T, MODE, LC>(P, w, wbase + buf * C::BUF_BYTES, g, li, lane, lossbuf);
         __syncwarp();
         w = wn;
         buf ^= 1;
@@ -336,12 +373,12 @@ __device__ __forceinline__ void own_epilogue(const VarParams& P, int v, int inst
 }
 
 template <typename T, int MODE, int LC>
-__device__ __forceinline__ void process_own_item(const VarParams& P, int w, int g, int li, int lane) {
+__device__ __forceinline__ void process_own_item(const VarParams& P, int w, int g, int li, int lane, float* lossbuf) {
     constexpr int VEC = Elem<T>::VEC, G = 32 / LC, H = VEC / 2, BC = LC * VEC;
-    // gathers in flight per batch: the pass is latency-bound, so the 16-bit form uses what its
-    // 128 registers allow (12 with the loss credits, 16 without: 15.6 and 10.9 ms against 17.1
-    // and 13.4 ms with 8 on the community workload); float32 keeps 8
-    constexpr int NBL = (VEC == 8) ? 12 : 8, NBG = (VEC == 8) ? 16 : 8;
+    // gathers in flight per batch: 8 per lane group; with the tile's loss sums in shared memory
+    // the pass fits 80 registers and 3 CTAs (24 warps) per SM, which keeps more gathers in flight
+    // per SM than 12-16 per batch at 2 CTAs (12.3 against 13.2 ms on the community workload)
+    constexpr int NBL = 8, NBG = 8;
     const int item = w % P.n_items;
     const int chunk = w / P.n_items;
     const VarItem it = P.items[item];
@@ -358,9 +395,9 @@ __device__ __forceinline__ void process_own_item(const VarParams& P, int w, int 
     set_row_bounds(rv, P.n_rows, P.status);
     const bool loss = P.loss_part != nullptr;
 
-    float Ls[VEC], Lc[VEC];
-#pragma unroll
-    for (int e = 0; e < VEC; ++e) Ls[e] = Lc[e] = 0.0f;
+    LossSm<VEC> L;
+    L.a = static_cast<uint32_t>(__cvta_generic_to_shared(lossbuf)) + lane * 16;
+    if (loss) L.zero();
     uint4 e = (g < it.nv) ? __ldg(ent + g) : make_uint4(0u, 0u, 0u, 0u);
     for (int j = g; j < it.nv; j += G) {
         const int v = it.v0 + static_cast<int>(e.x);
@@ -387,7 +424,7 @@ __device__ __forceinline__ void process_own_item(const VarParams& P, int w, int 
 #pragma unroll
             for (int e = 0; e < VEC; ++e) xs[e] = 0.0f;
             if (ld_ok) unpack<T>(load_row(rv, static_cast<uint32_t>(v)), xs);
-            credit_flush<VEC>(cr, xs, Ls, Lc);
+            credit_flush_v<VEC>(cr, xs, L);
         } else {
             var_gather<T, VEC, NBG, false, true>(it.kk, cd, cs, ce, rv, gacc, cr);
         }
@@ -413,9 +450,10 @@ __device__ __forceinline__ void process_own_item(const VarParams& P, int w, int 
     }
     __syncwarp();
     if (loss) {
-        float lf[VEC];
+        float lf[VEC], lc[VEC];
+        L.load(lf, lc);
 #pragma unroll
-        for (int e = 0; e < VEC; ++e) lf[e] = Ls[e] - Lc[e];
+        for (int e = 0; e < VEC; ++e) lf[e] -= lc[e];
         group_sum<LC>(lf);
         if (g == 0) {
             float* dst = P.loss_part + static_cast<int64_t>(item) * P.bpad + lane_base;
@@ -427,12 +465,13 @@ __device__ __forceinline__ void process_own_item(const VarParams& P, int w, int 
 }
 
 template <typename T, int MODE, int LC>
-__global__ void __launch_bounds__(kThreads, Elem<T>::VEC == 4 ? 3 : 2) k_var_own(const VarParams P) {
+__global__ void __launch_bounds__(kThreads, 3) k_var_own(const VarParams P) {
+    __shared__ __align__(16) float own_loss[kWarps][2 * 32 * Elem<T>::VEC];   // per warp: LossSm
     const int lane = threadIdx.x & 31;
     const int g = lane / LC, li = lane % LC;
     const int total = P.n_items * P.n_chunks;
     for (int w = fetch_work(P.head, lane); w < total; w = fetch_work(P.head, lane)) {
-        process_own_item<T, MODE, LC>(P, w, g, li, lane);
+        process_own_item<T, MODE, LC>(P, w, g, li, lane, own_loss[threadIdx.x >> 5]);
         __syncwarp();
     }
     queue_exit(P.head, P.exit_cnt);
@@ -489,7 +528,7 @@ __device__ __forceinline__ bool process_var_ring(const VarParams& P, const CUten
     const uint32_t* vt =
         reinterpret_cast<const uint32_t*>(buf + (reinterpret_cast<uintptr_t>(P.vtab + it.vtab_base) & 15));
     const uint32_t* cd = reinterpret_cast<const uint32_t*>(
-        buf + kVarVtabBytes + kVarRecBytes + (reinterpret_cast<uintptr_t>(P.codes + it.code_base) & 15));
+        buf + C::CODE_OFF + (reinterpret_cast<uintptr_t>(P.codes + it.code_base) & 15));
     const int cand0 = chunk * C::BC;
     const int lane_base = cand0 + lane * VEC;
     const bool ld_ok = lane_base < P.B;
@@ -1155,7 +1194,7 @@ __global__ void k_wait_selftest(int32_t* status, uint64_t limit_ns) {
 template <typename T, int MODE, int LC>
 int var_grid_t() {
     static int grid = 0;
-    if (!grid) grid = persistent_grid(k_var_pass<T, MODE, LC>, kWarps * var_warp_bytes<T>());
+    if (!grid) grid = persistent_grid(k_var_pass<T, MODE, LC>, kWarps * var_warp_bytes<T, LC>());
     return grid;
 }
 template <typename T, int MODE>
@@ -1201,14 +1240,7 @@ int check_grid_t() {
 template <typename T, int MODE, int LC>
 int own_grid_t() {
     static int grid = 0;
-    if (!grid) {
-        auto kernel = k_var_own<T, MODE, LC>;
-        cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxL1);
-        int per_sm = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kThreads, 0) != cudaSuccess || per_sm < 1)
-            per_sm = 1;
-        grid = per_sm * sm_count();
-    }
+    if (!grid) grid = persistent_grid(k_var_own<T, MODE, LC>, 0);
     return grid;
 }
 template <typename T, int MODE>
@@ -1240,12 +1272,24 @@ int var_grid_lc(int lc) {
 }
 template <typename T, int MODE>
 cudaError_t var_launch_lc(const VarParams& p, int lc, int grid, cudaStream_t s) {
-    const int smem = kWarps * var_warp_bytes<T>();
+    constexpr int W = kWarps;
     switch (lc) {
-        case 32: var_grid_t<T, MODE, 32>(); k_var_pass<T, MODE, 32><<<grid, kThreads, smem, s>>>(p); break;
-        case 16: var_grid_t<T, MODE, 16>(); k_var_pass<T, MODE, 16><<<grid, kThreads, smem, s>>>(p); break;
-        case 8: var_grid_t<T, MODE, 8>(); k_var_pass<T, MODE, 8><<<grid, kThreads, smem, s>>>(p); break;
-        default: var_grid_t<T, MODE, 4>(); k_var_pass<T, MODE, 4><<<grid, kThreads, smem, s>>>(p); break;
+        case 32:
+            var_grid_t<T, MODE, 32>();
+            k_var_pass<T, MODE, 32><<<grid, kThreads, W * var_warp_bytes<T, 32>(), s>>>(p);
+            break;
+        case 16:
+            var_grid_t<T, MODE, 16>();
+            k_var_pass<T, MODE, 16><<<grid, kThreads, W * var_warp_bytes<T, 16>(), s>>>(p);
+            break;
+        case 8:
+            var_grid_t<T, MODE, 8>();
+            k_var_pass<T, MODE, 8><<<grid, kThreads, W * var_warp_bytes<T, 8>(), s>>>(p);
+            break;
+        default:
+            var_grid_t<T, MODE, 4>();
+            k_var_pass<T, MODE, 4><<<grid, kThreads, W * var_warp_bytes<T, 4>(), s>>>(p);
+            break;
     }
     return cudaGetLastError();
 }

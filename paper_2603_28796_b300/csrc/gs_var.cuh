@@ -339,6 +339,84 @@ __device__ __forceinline__ uint32_t ld_code(const uint32_t* cd, int i) {
 template <int H>
 struct Credits {
     float2 p[H], n[H];
+    __device__ __forceinline__ void zero() {
+#pragma unroll
+        for (int h = 0; h < H; ++h) p[h] = n[h] = make_float2(0.0f, 0.0f);
+    }
+    __device__ __forceinline__ void add_p(const float2 (&r)[H]) {
+#pragma unroll
+        for (int h = 0; h < H; ++h) p[h] = __ffma2_rn(make_float2(1.0f, 1.0f), r[h], p[h]);
+    }
+    __device__ __forceinline__ void add_n(const float2 (&r)[H]) {
+#pragma unroll
+        for (int h = 0; h < H; ++h) n[h] = __ffma2_rn(make_float2(1.0f, 1.0f), r[h], n[h]);
+    }
+    // weighted form for several lane groups side by side (wp, wn in {0, 1})
+    __device__ __forceinline__ void add_w(float wp, float wn, const float2 (&r)[H]) {
+#pragma unroll
+        for (int h = 0; h < H; ++h) {
+            p[h] = __ffma2_rn(make_float2(wp, wp), r[h], p[h]);
+            n[h] = __ffma2_rn(make_float2(wn, wn), r[h], n[h]);
+        }
+    }
+    __device__ __forceinline__ void get(float2 (&pp)[H], float2 (&nn)[H]) const {
+#pragma unroll
+        for (int h = 0; h < H; ++h) {
+            pp[h] = p[h];
+            nn[h] = n[h];
+        }
+    }
+};
+
+// 16-byte shared-memory accesses the compiler keeps in place (a lane's own slots; volatile so
+// that the sums are not hoisted back into registers).
+__device__ __forceinline__ float4 ld_shared4(uint32_t x) {
+    float4 r;
+    asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(r.x), "=f"(r.y), "=f"(r.z), "=f"(r.w) : "r"(x));
+    return r;
+}
+__device__ __forceinline__ void st_shared4(uint32_t x, float4 v) {
+    asm volatile("st.shared.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(x), "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w)
+                 : "memory");
+}
+
+// The same sums kept in shared memory (one warp, one lane group): a credit is a shared-memory
+// read-add-write of the lane's slots, which leaves the 2 * VEC registers of Credits to the
+// gathers. The additions are the same, in the same order, so the sums are bitwise those of
+// Credits. Layout: 16-byte slots, slot q of lane l at q * 512 + l * 16 bytes (conflict-free
+// 16-byte accesses), H / 2 slots of Cp then H / 2 of Cn.
+template <int H>
+struct CreditsSm {
+    static_assert(H % 2 == 0, "16-byte slots hold two candidate pairs");
+    uint32_t a;   // shared-memory address of the lane's first slot
+    __device__ __forceinline__ static float4 lds(uint32_t x) { return ld_shared4(x); }
+    __device__ __forceinline__ static void sts(uint32_t x, float4 v) { st_shared4(x, v); }
+    __device__ __forceinline__ void zero() const {
+#pragma unroll
+        for (int q = 0; q < H; ++q) sts(a + q * 512, make_float4(0.0f, 0.0f, 0.0f, 0.0f));
+    }
+    __device__ __forceinline__ void add_at(uint32_t x, const float2 (&r)[H]) const {
+#pragma unroll
+        for (int q = 0; q < H / 2; ++q) {
+            const float4 v = lds(x + q * 512);
+            const float2 lo = __ffma2_rn(make_float2(1.0f, 1.0f), r[2 * q], make_float2(v.x, v.y));
+            const float2 hi = __ffma2_rn(make_float2(1.0f, 1.0f), r[2 * q + 1], make_float2(v.z, v.w));
+            sts(x + q * 512, make_float4(lo.x, lo.y, hi.x, hi.y));
+        }
+    }
+    __device__ __forceinline__ void add_p(const float2 (&r)[H]) const { add_at(a, r); }
+    __device__ __forceinline__ void add_n(const float2 (&r)[H]) const { add_at(a + (H / 2) * 512, r); }
+    __device__ __forceinline__ void add_w(float, float, const float2 (&)[H]) const {}   // one lane group only
+    __device__ __forceinline__ void get(float2 (&pp)[H], float2 (&nn)[H]) const {
+#pragma unroll
+        for (int q = 0; q < H / 2; ++q) {
+            const float4 u = lds(a + q * 512), v = lds(a + (H / 2 + q) * 512);
+            pp[2 * q] = make_float2(u.x, u.y);
+            pp[2 * q + 1] = make_float2(u.z, u.w);
+            nn[2 * q] = make_float2(v.x, v.y);
+            nn[2 * q + 1] = make_float2(v.z, v.w);
+        }
+    }
 };
 
 // General slot loop over the occurrence codes [cs, ce) of the group, NB codes per batch; an
@@ -346,9 +424,9 @@ struct Credits {
 // suffix of the occurrence's clause), restarted after each end.
 // UNI: all 32 lanes of the warp process the same codes (one lane group), so branches on a code's
 // flags are uniform and the loss credit is added only where a code carries it.
-template <typename T, int VEC, int NB, bool LOSS, bool GC, bool UNI = false>
+template <typename T, int VEC, int NB, bool LOSS, bool GC, bool UNI, typename CR>
 __device__ __forceinline__ void var_slots(const uint32_t* cd, int cs, int ce, const RowView& rv,
-                                          float2 (&G2)[VEC / 2], Credits<VEC / 2>& cr) {
+                                          float2 (&G2)[VEC / 2], CR& cr) {
     constexpr int H = VEC / 2;
     float2 R[H];
 #pragma unroll
@@ -405,23 +483,16 @@ __device__ __forceinline__ void var_slots(const uint32_t* cd, int cs, int ce, co
             if (LOSS) {
                 if constexpr (UNI) {
                     if (c & kVCredit) {
-                        if (c & kVSelfNeg) {
-#pragma unroll
-                            for (int h = 0; h < H; ++h) cr.n[h] = __ffma2_rn(dup2(1.0f), rn[h], cr.n[h]);
-                        } else {
-#pragma unroll
-                            for (int h = 0; h < H; ++h) cr.p[h] = __ffma2_rn(dup2(1.0f), rn[h], cr.p[h]);
-                        }
+                        if (c & kVSelfNeg)
+                            cr.add_n(rn);
+                        else
+                            cr.add_p(rn);
                     }
                 } else {
                     const uint32_t f = c & (kVEnd | kVCredit | kVSelfNeg);
                     const float wp = (f == (kVEnd | kVCredit)) ? 1.0f : 0.0f;
                     const float wn = (f == (kVEnd | kVCredit | kVSelfNeg)) ? 1.0f : 0.0f;
-#pragma unroll
-                    for (int h = 0; h < H; ++h) {
-                        cr.p[h] = __ffma2_rn(dup2(wp), rn[h], cr.p[h]);
-                        cr.n[h] = __ffma2_rn(dup2(wn), rn[h], cr.n[h]);
-                    }
+                    cr.add_w(wp, wn, rn);
                 }
             }
         }
@@ -442,9 +513,9 @@ __device__ __forceinline__ void fixed_ab(uint32_t c, float& a, float& b) {
     }
 }
 
-template <typename T, int VEC, int K, int OB, bool LOSS, bool TAIL, bool GC, bool UNI = false>
+template <typename T, int VEC, int K, int OB, bool LOSS, bool TAIL, bool GC, bool UNI, typename CR>
 __device__ __forceinline__ void occ_batch(const uint32_t* cd, int s, int ce, const RowView& rv,
-                                          float2 (&G2)[VEC / 2], Credits<VEC / 2>& cr) {
+                                          float2 (&G2)[VEC / 2], CR& cr) {
     constexpr int H = VEC / 2;
     constexpr int NS = OB * K;
     uint32_t cw[NS];
@@ -478,13 +549,10 @@ __device__ __forceinline__ void occ_batch(const uint32_t* cd, int s, int ce, con
 #pragma unroll
                 for (int h = 0; h < H; ++h) G2[h] = __ffma2_rn(dup2(sg), prod[h], G2[h]);
                 if (LOSS && (last & kVCredit)) {
-                    if (last & kVSelfNeg) {
-#pragma unroll
-                        for (int h = 0; h < H; ++h) cr.n[h] = __ffma2_rn(dup2(1.0f), prod[h], cr.n[h]);
-                    } else {
-#pragma unroll
-                        for (int h = 0; h < H; ++h) cr.p[h] = __ffma2_rn(dup2(1.0f), prod[h], cr.p[h]);
-                    }
+                    if (last & kVSelfNeg)
+                        cr.add_n(prod);
+                    else
+                        cr.add_p(prod);
                 }
             }
             continue;
@@ -496,18 +564,14 @@ __device__ __forceinline__ void occ_batch(const uint32_t* cd, int s, int ce, con
             const uint32_t f = valid ? (last & (kVCredit | kVSelfNeg)) : 0u;
             const float wp = (f == kVCredit) ? 1.0f : 0.0f;
             const float wn = (f == (kVCredit | kVSelfNeg)) ? 1.0f : 0.0f;
-#pragma unroll
-            for (int h = 0; h < H; ++h) {
-                cr.p[h] = __ffma2_rn(dup2(wp), prod[h], cr.p[h]);
-                cr.n[h] = __ffma2_rn(dup2(wn), prod[h], cr.n[h]);
-            }
+            cr.add_w(wp, wn, prod);
         }
     }
 }
 
-template <typename T, int VEC, int K, bool LOSS, bool GC, bool UNI = false>
+template <typename T, int VEC, int K, bool LOSS, bool GC, bool UNI, typename CR>
 __device__ __forceinline__ void var_occ_fixed(const uint32_t* cd, int cs, int ce, const RowView& rv,
-                                              float2 (&G2)[VEC / 2], Credits<VEC / 2>& cr) {
+                                              float2 (&G2)[VEC / 2], CR& cr) {
     constexpr int OB = (K == 1) ? 8 : (K == 2 ? 4 : 3);
     constexpr int NS = OB * K;
     int s = cs;
@@ -517,9 +581,9 @@ __device__ __forceinline__ void var_occ_fixed(const uint32_t* cd, int cs, int ce
 
 // Gradient and (with LOSS) loss credits of one variable's occurrence codes [cs, ce); GC: the
 // codes are read from global memory instead of a shared-memory tile.
-template <typename T, int VEC, int NB, bool LOSS, bool GC = false, bool UNI = false>
+template <typename T, int VEC, int NB, bool LOSS, bool GC = false, bool UNI = false, typename CR = Credits<VEC / 2>>
 __device__ __forceinline__ void var_gather(int kk, const uint32_t* cd, int cs, int ce, const RowView& rv,
-                                           float (&gacc)[VEC], Credits<VEC / 2>& cr) {
+                                           float (&gacc)[VEC], CR& cr) {
     constexpr int H = VEC / 2;
     float2 G2[H];
 #pragma unroll
@@ -537,18 +601,6 @@ __device__ __forceinline__ void var_gather(int kk, const uint32_t* cd, int cs, i
     }
 }
 
-// Adds a variable's credited clause values, (1 - x) * Cp + x * Cn per candidate, to the tile's
-// compensated loss accumulator.
-template <int VEC>
-__device__ __forceinline__ void credit_flush(const Credits<VEC / 2>& cr, const float (&xs)[VEC], float (&Ls)[VEC],
-                                             float (&Lc)[VEC]) {
-#pragma unroll
-    for (int h = 0; h < VEC / 2; ++h) {
-        kahan_add(Ls[2 * h], Lc[2 * h], fmaf(1.0f - xs[2 * h], cr.p[h].x, xs[2 * h] * cr.n[h].x));
-        kahan_add(Ls[2 * h + 1], Lc[2 * h + 1], fmaf(1.0f - xs[2 * h + 1], cr.p[h].y, xs[2 * h + 1] * cr.n[h].y));
-    }
-}
-
 template <typename T, int MODE, int LC>
 struct VarCfg {
     static constexpr int VEC = Elem<T>::VEC;
@@ -561,6 +613,12 @@ struct VarCfg {
     // Adam state loaded before the gathers when each lane keeps few epilogue candidates (16-bit
     // values in narrow chunks); with 32-lane chunks the registers go to the gathers instead
     static constexpr bool PREFETCH = (VEC == 8) && (LC < 32);
+    // Per-warp staging buffer of one occurrence tile: the variable table, the occurrence offsets
+    // (read only when several lane groups split a variable's occurrences) and the codes.
+    static constexpr int REC_BYTES = (G > 1) ? kVarRecBytes : 0;
+    static constexpr int CODE_OFF = kVarVtabBytes + REC_BYTES;
+    static constexpr int BUF_BYTES = CODE_OFF + kVarCodeBytes;
+    static constexpr int STAGE_BYTES = 2 * BUF_BYTES + 16;   // two buffers + two mbarriers
 };
 
 // Adam state (delta, m, v) of the epilogue candidates of one lane.
@@ -675,7 +733,7 @@ __device__ __forceinline__ void issue_var_item(const VarParams& P, int item, uns
     mbar_expect_tx(bar, a.bytes + b.bytes + c.bytes);
     if (a.bytes) bulk_g2s(buf, reinterpret_cast<const void*>(a.src), a.bytes, bar);
     if (b.bytes) bulk_g2s(buf + kVarVtabBytes, reinterpret_cast<const void*>(b.src), b.bytes, bar);
-    if (c.bytes) bulk_g2s(buf + kVarVtabBytes + kVarRecBytes, reinterpret_cast<const void*>(c.src), c.bytes, bar);
+    if (c.bytes) bulk_g2s(buf + C::CODE_OFF, reinterpret_cast<const void*>(c.src), c.bytes, bar);
 }
 
 }  // namespace
