@@ -156,12 +156,25 @@ bool capturing(cudaStream_t s) {
 // instances) to fill the GPU a few times over, but no segment shorter than 32 tiles, and at
 // most 256 (a formula of 400,000 tiles and one slice gets 256 segments of ~1,600 tiles; 2,000
 // tiles and 32 slices get 19). max_tiles: the largest per-instance tile count of the list.
+// These are the segments of the forward tiles (clause-major loss and the exact check, whose
+// final count kernel walks the segments one thread per candidate).
 constexpr int32_t kMaxSegments = 256;
 int32_t n_segments(const gs_problem* p, int32_t B, int32_t max_tiles) {
     const int64_t slices = static_cast<int64_t>((std::max(B, 1) + 31) / 32) * std::max(p->h.n_inst, 1);
     const int64_t fill = (4LL * p->sms + slices - 1) / slices;
     const int64_t want = std::min<int64_t>(fill, (static_cast<int64_t>(max_tiles) + 31) / 32);
     return static_cast<int32_t>(std::min<int64_t>(kMaxSegments, std::max<int64_t>(1, want)));
+}
+// Segments of the variable-pass loss partials (one partial per occurrence tile or owned item,
+// up to a few hundred thousand per formula): the stage-1 walk is a chain of dependent loads per
+// warp, so these aim at 16 blocks per SM and allow up to 1,024 segments, still no segment
+// shorter than 32 tiles; the final loss kernel spreads the segments over 32 warps.
+constexpr int32_t kMaxLossSegments = 1024;
+int32_t n_loss_segments(const gs_problem* p, int32_t B, int32_t max_tiles) {
+    const int64_t slices = static_cast<int64_t>((std::max(B, 1) + 31) / 32) * std::max(p->h.n_inst, 1);
+    const int64_t fill = (16LL * p->sms + slices - 1) / slices;
+    const int64_t want = std::min<int64_t>(fill, (static_cast<int64_t>(max_tiles) + 31) / 32);
+    return static_cast<int32_t>(std::min<int64_t>(kMaxLossSegments, std::max<int64_t>(1, want)));
 }
 int32_t max_list(const std::vector<int32_t>& iptr) {
     int32_t mx = 0;
@@ -229,8 +242,8 @@ gs_status ensure_ws(gs_problem* p, int dtype, int32_t B, bool need_bits, cudaStr
         return st;
     if ((st = grow(&p->stage, &p->stage_cap,
                    std::max<size_t>(1, static_cast<size_t>(std::max({n_segments(p, B, max_list(p->h.f_iptr)),
-                                                                      n_segments(p, B, max_list(p->h.v_iptr)),
-                                                                      n_segments(p, B, max_list(p->h.o_iptr))})) *
+                                                                      n_loss_segments(p, B, max_list(p->h.v_iptr)),
+                                                                      n_loss_segments(p, B, max_list(p->h.o_iptr))})) *
                                            std::max(p->h.n_inst, 1) * std::max(B, 1)),
                    s, cap, "reduction stage")) != GS_OK)
         return st;
@@ -533,7 +546,8 @@ gs_status var_pass(gs_problem* p, int mode, const void* x_in, int dtype, int32_t
     if (loss)
         GS_CUDA(launch_loss_reduce2(p->part, c.bpad, own ? p->o_iptr : p->v_iptr, own ? p->o_list : p->v_list,
                                     p->inst_empty, p->h.n_inst, B,
-                                    n_segments(p, B, max_list(own ? p->h.o_iptr : p->h.v_iptr)), p->stage, loss, s),
+                                    n_loss_segments(p, B, max_list(own ? p->h.o_iptr : p->h.v_iptr)), p->stage, loss,
+                                    s),
                 "loss reduce launch");
     return GS_OK;
 }

@@ -1068,25 +1068,25 @@ __global__ void __launch_bounds__(256) k_reduce_tiles(const PT* part, int32_t st
     }
 }
 
-// Stage 2 of the loss: block (32-candidate slice, instance); its 8 warps sum the segments
+// Stage 2 of the loss: block (32-candidate slice, instance); its 32 warps sum the segments
 // round-robin, then combine in warp order; empty clauses (product 1 each) are added.
-__global__ void __launch_bounds__(256) k_loss_final(const double* stage, int32_t n_seg, int32_t n_inst,
-                                                    const int64_t* n_empty, int32_t B, double* loss) {
-    __shared__ double red[8][32];
+__global__ void __launch_bounds__(1024) k_loss_final(const double* stage, int32_t n_seg, int32_t n_inst,
+                                                     const int64_t* n_empty, int32_t B, double* loss) {
+    __shared__ double red[32][32];
     const int inst = blockIdx.y;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int b = blockIdx.x * 32 + lane;
     double t = 0.0;
     if (b < B) {
 #pragma unroll 4
-        for (int sgm = warp; sgm < n_seg; sgm += 8) t += stage[(static_cast<int64_t>(sgm) * n_inst + inst) * B + b];
+        for (int sgm = warp; sgm < n_seg; sgm += 32) t += stage[(static_cast<int64_t>(sgm) * n_inst + inst) * B + b];
     }
     red[warp][lane] = t;
     __syncthreads();
     if (warp == 0 && b < B) {
         double u = 0.0;
 #pragma unroll
-        for (int q = 0; q < 8; ++q) u += red[q][lane];
+        for (int q = 0; q < 32; ++q) u += red[q][lane];
         loss[static_cast<int64_t>(inst) * B + b] = u + static_cast<double>(n_empty[inst]);
     }
 }
@@ -1441,7 +1441,7 @@ cudaError_t launch_loss_reduce2(const float* part, int32_t bpad, const int32_t* 
     if (B <= 0 || n_inst <= 0) return cudaSuccess;
     k_reduce_tiles<float, double><<<dim3((B + 31) / 32, n_inst, n_seg), 256, 0, s>>>(part, bpad, iptr, items, B,
                                                                                       n_seg, stage);
-    k_loss_final<<<dim3((B + 31) / 32, n_inst), 256, 0, s>>>(stage, n_seg, n_inst, n_empty, B, loss);
+    k_loss_final<<<dim3((B + 31) / 32, n_inst), 1024, 0, s>>>(stage, n_seg, n_inst, n_empty, B, loss);
     return cudaGetLastError();
 }
 

@@ -465,6 +465,13 @@ __device__ __forceinline__ void var_slots(const uint32_t* cd, int cs, int ce, co
                         G2[h] = __ffma2_rn(dup2(sg), rn[h], G2[h]);
                         R[h] = dup2(1.0f);
                     }
+                    // a credit sits on an occurrence's last code, so it is tested only there
+                    if (LOSS && (c & kVCredit)) {
+                        if (c & kVSelfNeg)
+                            cr.add_n(rn);
+                        else
+                            cr.add_p(rn);
+                    }
                 } else {
 #pragma unroll
                     for (int h = 0; h < H; ++h) R[h] = rn[h];
@@ -481,14 +488,7 @@ __device__ __forceinline__ void var_slots(const uint32_t* cd, int cs, int ce, co
                 }
             }
             if (LOSS) {
-                if constexpr (UNI) {
-                    if (c & kVCredit) {
-                        if (c & kVSelfNeg)
-                            cr.add_n(rn);
-                        else
-                            cr.add_p(rn);
-                    }
-                } else {
+                if constexpr (!UNI) {
                     const uint32_t f = c & (kVEnd | kVCredit | kVSelfNeg);
                     const float wp = (f == (kVEnd | kVCredit)) ? 1.0f : 0.0f;
                     const float wn = (f == (kVEnd | kVCredit | kVSelfNeg)) ? 1.0f : 0.0f;
