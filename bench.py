@@ -43,6 +43,9 @@ def parse():
                     help="shrink the workload's formula (n and m) by this factor, for profiling small cases")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--launch", choices=["graph", "eager"], default="graph",
+                    help="graph: the K timed steps are captured once in a CUDA graph and replayed once in the "
+                         "timed region (the engine's own run loop); eager: one host call per kernel launch")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle sample")
     ap.add_argument("--no-autotune", action="store_true", help="skip gs_autotune (use defaults / --var-* flags)")
     ap.add_argument("--legs", default="st,pool,precision,tseitin,plain,structured,batching",
@@ -685,7 +688,36 @@ def run_native(args):
     torch.cuda.synchronize()
 
     K = args.steps
-    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(K)]
+
+    def record_steps(ev):
+        for k in range(K):
+            e0, e1, e2 = ev[k]
+            eng.t += 1
+            e0.record()
+            _abi.gs_step(prob, eng.delta, eng.m, eng.v, eng.t, x_in=eng.x[eng.cur], x_out=eng.x[eng.cur ^ 1],
+                         loss=eng.loss, bits=eng.bits)
+            e1.record()
+            eng.cur ^= 1
+            _abi.gs_check_bits(prob, eng.bits, B, eng.unsat, eng.best)
+            e2.record()
+
+    graph = None
+    if args.launch == "graph":
+        # The K timed steps (each: gs_step, then gs_check_bits), with the per-step timing events
+        # as event-record nodes, are captured before the timed region; capture runs nothing.
+        ev = [[torch.cuda.Event(enable_timing=True, external=True) for _ in range(3)] for _ in range(K)]
+        t0, cur0 = eng.t, eng.cur
+        graph = torch.cuda.CUDAGraph()
+        cap = torch.cuda.Stream()
+        cap.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(cap):
+            with torch.cuda.graph(graph, stream=cap):
+                record_steps(ev)
+        torch.cuda.current_stream().wait_stream(cap)
+        eng_after = (eng.t, eng.cur)
+        eng.t, eng.cur = t0, cur0
+    else:
+        ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(K)]
     sampler = ClockSampler(dev.index if dev.index is not None else 0)
     if world > 1:
         dist.barrier()
@@ -694,18 +726,15 @@ def run_native(args):
     t_start = torch.cuda.Event(enable_timing=True)
     t_end = torch.cuda.Event(enable_timing=True)
     t_start.record()
-    for k in range(K):
-        e0, e1, e2 = ev[k]
-        eng.t += 1
-        e0.record()
-        _abi.gs_step(prob, eng.delta, eng.m, eng.v, eng.t, x_in=eng.x[eng.cur], x_out=eng.x[eng.cur ^ 1],
-                     loss=eng.loss, bits=eng.bits)
-        e1.record()
-        eng.cur ^= 1
-        _abi.gs_check_bits(prob, eng.bits, B, eng.unsat, eng.best)
-        e2.record()
+    if graph is not None:
+        graph.replay()
+    else:
+        record_steps(ev)
     t_end.record()
     torch.cuda.synchronize()
+    if graph is not None:
+        eng.t, eng.cur = eng_after
+        del graph
     clocks = sampler.stop()
     if world > 1:
         dist.barrier()
@@ -862,6 +891,8 @@ def run_native(args):
                    "l2": "inputs larger than L2: x %.0f MB + delta/m/v %.0f MB per step" % (
                        n * B * s_bytes / 1e6, n * B * 12 / 1e6),
                    "steps_per_s": 1000.0 * K / total_ms, "tuning": tuning,
+                   "launch": ("cuda_graph: the K steps captured once, replayed once in the timed region"
+                              if args.launch == "graph" else "eager: one host call per kernel launch"),
                    "plan": {k: info[k] for k in ("fwd_tile_codes", "var_tile_codes", "own_item_codes")},
                    "tuning_source": tune_rec["source"] if tune_rec else "flags", "best_after_run": best},
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "gpu_launches": launches_per_step * K,

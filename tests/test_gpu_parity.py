@@ -120,6 +120,14 @@ def test_fused_step(name, B, dtype, gather):
     check_fused_step(name, B, dtype, var_gather=gather)
 
 
+@pytest.mark.parametrize("B", [200, 300])
+@pytest.mark.parametrize("name", ["3sat", "mixed", "edge", "community"])
+def test_fused_step_f16_wide_chunks(name, B):
+    """FP16 storage with 32-lane chunks (the variable's loss credits kept in shared memory; one
+    partial chunk at B = 200, a full and a partial one at B = 300)."""
+    check_fused_step(name, B, "f16")
+
+
 @pytest.mark.parametrize("split", [1, 2])
 @pytest.mark.parametrize("lanes", [4, 8])
 @pytest.mark.parametrize("dtype", ["f32", "bf16", "f16"])
