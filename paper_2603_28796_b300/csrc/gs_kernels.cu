@@ -153,12 +153,12 @@ __device__ __forceinline__ void process_var_item(const VarParams& P, int w, cons
                 // the variable's own value (for its loss credits) is requested with the gathers
                 uint4 own_raw = make_uint4(0u, 0u, 0u, 0u);
                 if (ld_ok) own_raw = load_row(rv, static_cast<uint32_t>(v));
-                var_gather<T, VEC, C::NB, true, false, (C::G == 1)>(it.kk, cd, cs, ce, rv, gacc, cr);
+                var_gather<T, VEC, C::NB, true, false, (C::G == 1)>(it.kk, cd, cs, ce, ce, rv, gacc, cr);
                 float xs[VEC];
                 unpack<T>(own_raw, xs);
                 credit_flush_v<VEC>(cr, xs, L);
             } else {
-                var_gather<T, VEC, C::NB, false, false, (C::G == 1)>(it.kk, cd, cs, ce, rv, gacc, cr);
+                var_gather<T, VEC, C::NB, false, false, (C::G == 1)>(it.kk, cd, cs, ce, ce, rv, gacc, cr);
             }
             group_sum<LC>(gacc);
             float ge[VPG];
@@ -187,14 +187,14 @@ __device__ __forceinline__ void process_var_item(const VarParams& P, int w, cons
         CR cr = cr0;
         if (credits_in_smem<T, LC>() && loss) cr.zero();
         if (loss) {
-            var_gather<T, VEC, C::NB, true, false, (C::G == 1)>(it.kk, cd, cs, ce, rv, gacc, cr);
+            var_gather<T, VEC, C::NB, true, false, (C::G == 1)>(it.kk, cd, cs, ce, ce, rv, gacc, cr);
             float xs[VEC];
 #pragma unroll
             for (int e = 0; e < VEC; ++e) xs[e] = 0.0f;
             if (ld_ok) unpack<T>(load_row(rv, static_cast<uint32_t>(v)), xs);
             credit_flush_v<VEC>(cr, xs, L);
         } else {
-            var_gather<T, VEC, C::NB, false, false, (C::G == 1)>(it.kk, cd, cs, ce, rv, gacc, cr);
+            var_gather<T, VEC, C::NB, false, false, (C::G == 1)>(it.kk, cd, cs, ce, ce, rv, gacc, cr);
         }
         group_sum<LC>(gacc);
         float* rowp = P.split_part + static_cast<int64_t>(it.split_row + it.part) * P.bpad + lane_base;
@@ -419,14 +419,14 @@ __device__ __forceinline__ void process_own_item(const VarParams& P, int w, int 
 #pragma unroll
         for (int h = 0; h < H; ++h) cr.p[h] = cr.n[h] = dup2(0.0f);
         if (loss) {
-            var_gather<T, VEC, NBL, true, true>(it.kk, cd, cs, ce, rv, gacc, cr);
+            var_gather<T, VEC, NBL, true, true>(it.kk, cd, cs, ce, static_cast<int>(e.w), rv, gacc, cr);
             float xs[VEC];
 #pragma unroll
             for (int e = 0; e < VEC; ++e) xs[e] = 0.0f;
             if (ld_ok) unpack<T>(load_row(rv, static_cast<uint32_t>(v)), xs);
             credit_flush_v<VEC>(cr, xs, L);
         } else {
-            var_gather<T, VEC, NBG, false, true>(it.kk, cd, cs, ce, rv, gacc, cr);
+            var_gather<T, VEC, NBG, false, true>(it.kk, cd, cs, ce, ce, rv, gacc, cr);
         }
         AdamState<VEC> st;
         if constexpr (MODE == kModeAdam) {

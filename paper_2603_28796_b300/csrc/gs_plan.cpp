@@ -365,6 +365,31 @@ gs_status build_var(const int64_t* clause_ptr, const int32_t* lits, HostPlan& P)
         code_pos[row] += c;
     });
     std::vector<int64_t>().swap(code_pos);
+    // Each variable's credited occurrences (the clause's loss credit sits at this literal) are
+    // moved to the front of its list, keeping the clause order within both parts; credit_len is
+    // the credited part's code count. The owned-variable pass runs the credit arithmetic only
+    // over that part (the fourth field of its item entries marks where it ends).
+    std::vector<int64_t> credit_len(n, 0);
+    parallel_blocks(n, [&](int64_t v0, int64_t v1, int) {
+        std::vector<uint32_t> tmp;
+        for (int64_t v = v0; v < v1; ++v) {
+            uint32_t* c = P.vcodes.data() + code_start[v];
+            const int64_t len = code_start[v + 1] - code_start[v];
+            tmp.assign(c, c + len);
+            int64_t out = 0;
+            for (int pass = 0; pass < 2; ++pass) {
+                for (int64_t q = 0; q < len;) {
+                    int64_t e = q;
+                    while (!(tmp[e] & kVEnd)) ++e;
+                    const bool credited = (tmp[e] & kVCredit) != 0u;
+                    if (credited == (pass == 0))
+                        for (int64_t r = q; r <= e; ++r) c[out++] = tmp[r];
+                    q = e + 1;
+                }
+                if (pass == 0) credit_len[v] = out;
+            }
+        }
+    });
     const uint32_t* codes = P.vcodes.data();
 
     // Sequential partition into tiles (creation order = storage order of recs and vtab).
@@ -544,7 +569,7 @@ gs_status build_var(const int64_t* clause_ptr, const int32_t* lits, HostPlan& P)
                 P.oent.push_back(static_cast<uint32_t>(i));
                 P.oent.push_back(static_cast<uint32_t>(code_start[v] - cur.code_base));
                 P.oent.push_back(static_cast<uint32_t>(code_start[v + 1] - cur.code_base));
-                P.oent.push_back(0u);
+                P.oent.push_back(static_cast<uint32_t>(code_start[v] + credit_len[v] - cur.code_base));
             }
             cur.kk = (kk >= 1 && kk <= 3) ? kk : 0;
             P.oitems.push_back(cur);

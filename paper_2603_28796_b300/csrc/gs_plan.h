@@ -36,8 +36,9 @@ struct HostPlan {
     std::vector<VarItem> vitems;
     int32_t n_split = 0, n_split_rows = 0;
     // variable-owned items: runs of whole variables (codes shared with the occurrence tiles);
-    // oent holds one 4 x uint32 entry per variable {row - v0, first code, end code, 0} (codes
-    // relative to the item's first code) in the order the lane groups take them
+    // oent holds one 4 x uint32 entry per variable {row - v0, first code, end code, end of the
+    // credited occurrences' codes} (codes relative to the item's first code) in the order the
+    // lane groups take them
     std::vector<uint32_t> oent;
     std::vector<VarItem> oitems;
     bool own_ok = true;   // false if a variable has too many codes for an item's 32-bit counts

@@ -1,8 +1,7 @@
-// Device helpers of the variable-major pass shared by its kernel translation units
-// (gs_kernels.cu: tiled, owned-variable and TMA-ring forms; gs_stream.cu: streaming form):
-// element types and vector loads/stores with L2 cache hints, literal factors, the leave-one-out
-// occurrence loops, loss credits, the Adam epilogue and the tile staging. Internal linkage in
-// each unit.
+// Device helpers of the variable-major pass (its tiled, owned-variable and TMA-ring forms in
+// gs_kernels.cu): element types, gathers and streaming-operator loads/stores, literal factors,
+// the leave-one-out occurrence loops, loss credits (in registers or shared memory), the Adam
+// epilogue and the tile staging layout. Internal linkage.
 #pragma once
 #include <cuda.h>
 #include <cuda_bf16.h>
@@ -419,83 +418,99 @@ struct CreditsSm {
     }
 };
 
-// General slot loop over the occurrence codes [cs, ce) of the group, NB codes per batch; an
+// One batch of the general slot loop: NB occurrence codes from s (up to ce) of the group; an
 // occurrence ends at a code carrying kVEnd. R is the running leave-one-out product (prefix then
 // suffix of the occurrence's clause), restarted after each end.
 // UNI: all 32 lanes of the warp process the same codes (one lane group), so branches on a code's
 // flags are uniform and the loss credit is added only where a code carries it.
 template <typename T, int VEC, int NB, bool LOSS, bool GC, bool UNI, typename CR>
-__device__ __forceinline__ void var_slots(const uint32_t* cd, int cs, int ce, const RowView& rv,
+__device__ __forceinline__ void slot_batch(const uint32_t* cd, int s, int ce, const RowView& rv, float2 (&R)[VEC / 2],
+                                           float2 (&G2)[VEC / 2], CR& cr) {
+    constexpr int H = VEC / 2;
+    uint32_t cw[NB];
+    uint4 raw[NB];
+    if constexpr (GC) {
+        if (s + 32 < ce) prefetch_l1(cd + s + 32);   // the codes four batches ahead
+    }
+#pragma unroll
+    for (int j = 0; j < NB; ++j) cw[j] = (s + j < ce) ? ld_code<GC>(cd, s + j) : (kVSentinel << kVShift);
+#pragma unroll
+    for (int j = 0; j < NB; ++j) {
+        const uint32_t u = cw[j] >> kVShift;
+        raw[j] = make_uint4(0u, 0u, 0u, 0u);
+        if (rv.ok && u != kVSentinel) raw[j] = load_row(rv, u);
+    }
+#pragma unroll
+    for (int j = 0; j < NB; ++j) {
+        const uint32_t c = cw[j];
+        float a, b;
+        code_ab(c, a, b);
+        float2 f[H];
+        factors<T>(raw[j], a, b, f);
+        const bool end = (c & kVEnd) != 0u;
+        float2 rn[H];
+        if constexpr (UNI) {
+            // one lane group: the end of an occurrence is a uniform branch
+#pragma unroll
+            for (int h = 0; h < H; ++h) rn[h] = __fmul2_rn(R[h], f[h]);
+            if (end) {
+                const float sg = occ_sign(c);
+#pragma unroll
+                for (int h = 0; h < H; ++h) {
+                    G2[h] = __ffma2_rn(dup2(sg), rn[h], G2[h]);
+                    R[h] = dup2(1.0f);
+                }
+                // a credit sits on an occurrence's last code, so it is tested only there
+                if (LOSS && (c & kVCredit)) {
+                    if (c & kVSelfNeg)
+                        cr.add_n(rn);
+                    else
+                        cr.add_p(rn);
+                }
+            } else {
+#pragma unroll
+                for (int h = 0; h < H; ++h) R[h] = rn[h];
+            }
+        } else {
+            const float sg = end ? occ_sign(c) : 0.0f;
+            const float e1 = end ? 1.0f : 0.0f;   // restart the running product after an end:
+            const float keep = 1.0f - e1;         // R = rn * keep + e1 (rn is finite)
+#pragma unroll
+            for (int h = 0; h < H; ++h) {
+                rn[h] = __fmul2_rn(R[h], f[h]);
+                G2[h] = __ffma2_rn(dup2(sg), rn[h], G2[h]);
+                R[h] = __ffma2_rn(rn[h], dup2(keep), dup2(e1));
+            }
+        }
+        if (LOSS) {
+            if constexpr (!UNI) {
+                const uint32_t f = c & (kVEnd | kVCredit | kVSelfNeg);
+                const float wp = (f == (kVEnd | kVCredit)) ? 1.0f : 0.0f;
+                const float wn = (f == (kVEnd | kVCredit | kVSelfNeg)) ? 1.0f : 0.0f;
+                cr.add_w(wp, wn, rn);
+            }
+        }
+    }
+}
+
+// The general slot loop over the group's occurrence codes [cs, ce). With several lane groups
+// the credits are predicated arithmetic on every code, so the loop is split: the credited
+// occurrences come first in each variable's list, ending at cc, and batches run with the credit
+// arithmetic only while some group of the warp is still before its cc.
+template <typename T, int VEC, int NB, bool LOSS, bool GC, bool UNI, typename CR>
+__device__ __forceinline__ void var_slots(const uint32_t* cd, int cs, int ce, int cc, const RowView& rv,
                                           float2 (&G2)[VEC / 2], CR& cr) {
     constexpr int H = VEC / 2;
     float2 R[H];
 #pragma unroll
     for (int h = 0; h < H; ++h) R[h] = dup2(1.0f);
-    for (int s = cs; s < ce; s += NB) {
-        uint32_t cw[NB];
-        uint4 raw[NB];
-        if constexpr (GC) {
-            if (s + 32 < ce) prefetch_l1(cd + s + 32);   // the codes four batches ahead
-        }
-#pragma unroll
-        for (int j = 0; j < NB; ++j) cw[j] = (s + j < ce) ? ld_code<GC>(cd, s + j) : (kVSentinel << kVShift);
-#pragma unroll
-        for (int j = 0; j < NB; ++j) {
-            const uint32_t u = cw[j] >> kVShift;
-            raw[j] = make_uint4(0u, 0u, 0u, 0u);
-            if (rv.ok && u != kVSentinel) raw[j] = load_row(rv, u);
-        }
-#pragma unroll
-        for (int j = 0; j < NB; ++j) {
-            const uint32_t c = cw[j];
-            float a, b;
-            code_ab(c, a, b);
-            float2 f[H];
-            factors<T>(raw[j], a, b, f);
-            const bool end = (c & kVEnd) != 0u;
-            float2 rn[H];
-            if constexpr (UNI) {
-                // one lane group: the end of an occurrence is a uniform branch
-#pragma unroll
-                for (int h = 0; h < H; ++h) rn[h] = __fmul2_rn(R[h], f[h]);
-                if (end) {
-                    const float sg = occ_sign(c);
-#pragma unroll
-                    for (int h = 0; h < H; ++h) {
-                        G2[h] = __ffma2_rn(dup2(sg), rn[h], G2[h]);
-                        R[h] = dup2(1.0f);
-                    }
-                    // a credit sits on an occurrence's last code, so it is tested only there
-                    if (LOSS && (c & kVCredit)) {
-                        if (c & kVSelfNeg)
-                            cr.add_n(rn);
-                        else
-                            cr.add_p(rn);
-                    }
-                } else {
-#pragma unroll
-                    for (int h = 0; h < H; ++h) R[h] = rn[h];
-                }
-            } else {
-                const float sg = end ? occ_sign(c) : 0.0f;
-                const float e1 = end ? 1.0f : 0.0f;   // restart the running product after an end:
-                const float keep = 1.0f - e1;         // R = rn * keep + e1 (rn is finite)
-#pragma unroll
-                for (int h = 0; h < H; ++h) {
-                    rn[h] = __fmul2_rn(R[h], f[h]);
-                    G2[h] = __ffma2_rn(dup2(sg), rn[h], G2[h]);
-                    R[h] = __ffma2_rn(rn[h], dup2(keep), dup2(e1));
-                }
-            }
-            if (LOSS) {
-                if constexpr (!UNI) {
-                    const uint32_t f = c & (kVEnd | kVCredit | kVSelfNeg);
-                    const float wp = (f == (kVEnd | kVCredit)) ? 1.0f : 0.0f;
-                    const float wn = (f == (kVEnd | kVCredit | kVSelfNeg)) ? 1.0f : 0.0f;
-                    cr.add_w(wp, wn, rn);
-                }
-            }
-        }
+    int s = cs;
+    if constexpr (LOSS && !UNI) {
+        for (; s < ce && __any_sync(__activemask(), s < cc); s += NB)
+            slot_batch<T, VEC, NB, true, GC, UNI>(cd, s, ce, rv, R, G2, cr);
+        for (; s < ce; s += NB) slot_batch<T, VEC, NB, false, GC, UNI>(cd, s, ce, rv, R, G2, cr);
+    } else {
+        for (; s < ce; s += NB) slot_batch<T, VEC, NB, LOSS, GC, UNI>(cd, s, ce, rv, R, G2, cr);
     }
 }
 
@@ -579,10 +594,12 @@ __device__ __forceinline__ void var_occ_fixed(const uint32_t* cd, int cs, int ce
     if (s < ce) occ_batch<T, VEC, K, OB, LOSS, true, GC, UNI>(cd, s, ce, rv, G2, cr);
 }
 
-// Gradient and (with LOSS) loss credits of one variable's occurrence codes [cs, ce); GC: the
-// codes are read from global memory instead of a shared-memory tile.
+// Gradient and (with LOSS) loss credits of one variable's occurrence codes [cs, ce); the
+// credited occurrences lie in [cs, cc) (cc = ce when that is not known: every code is then
+// checked for a credit); GC: the codes are read from global memory instead of a shared-memory
+// tile.
 template <typename T, int VEC, int NB, bool LOSS, bool GC = false, bool UNI = false, typename CR = Credits<VEC / 2>>
-__device__ __forceinline__ void var_gather(int kk, const uint32_t* cd, int cs, int ce, const RowView& rv,
+__device__ __forceinline__ void var_gather(int kk, const uint32_t* cd, int cs, int ce, int cc, const RowView& rv,
                                            float (&gacc)[VEC], CR& cr) {
     constexpr int H = VEC / 2;
     float2 G2[H];
@@ -592,7 +609,7 @@ __device__ __forceinline__ void var_gather(int kk, const uint32_t* cd, int cs, i
         case 1: var_occ_fixed<T, VEC, 1, LOSS, GC, UNI>(cd, cs, ce, rv, G2, cr); break;
         case 2: var_occ_fixed<T, VEC, 2, LOSS, GC, UNI>(cd, cs, ce, rv, G2, cr); break;
         case 3: var_occ_fixed<T, VEC, 3, LOSS, GC, UNI>(cd, cs, ce, rv, G2, cr); break;
-        default: var_slots<T, VEC, NB, LOSS, GC, UNI>(cd, cs, ce, rv, G2, cr); break;
+        default: var_slots<T, VEC, NB, LOSS, GC, UNI>(cd, cs, ce, cc, rv, G2, cr); break;
     }
 #pragma unroll
     for (int h = 0; h < H; ++h) {
