@@ -585,12 +585,20 @@ __device__ __forceinline__ void occ_batch(const uint32_t* cd, int s, int ce, con
 }
 
 template <typename T, int VEC, int K, bool LOSS, bool GC, bool UNI, typename CR>
-__device__ __forceinline__ void var_occ_fixed(const uint32_t* cd, int cs, int ce, const RowView& rv,
+__device__ __forceinline__ void var_occ_fixed(const uint32_t* cd, int cs, int ce, int cc, const RowView& rv,
                                               float2 (&G2)[VEC / 2], CR& cr) {
     constexpr int OB = (K == 1) ? 8 : (K == 2 ? 4 : 3);
     constexpr int NS = OB * K;
     int s = cs;
-    for (; s + NS <= ce; s += NS) occ_batch<T, VEC, K, OB, LOSS, false, GC, UNI>(cd, s, ce, rv, G2, cr);
+    if constexpr (LOSS && !UNI && K >= 3) {
+        // as in var_slots: the credit arithmetic only while some lane group is before its cc
+        // (for width-3 clauses the credited third of the list is too short to pay for the vote)
+        for (; s + NS <= ce && __any_sync(__activemask(), s < cc); s += NS)
+            occ_batch<T, VEC, K, OB, true, false, GC, UNI>(cd, s, ce, rv, G2, cr);
+        for (; s + NS <= ce; s += NS) occ_batch<T, VEC, K, OB, false, false, GC, UNI>(cd, s, ce, rv, G2, cr);
+    } else {
+        for (; s + NS <= ce; s += NS) occ_batch<T, VEC, K, OB, LOSS, false, GC, UNI>(cd, s, ce, rv, G2, cr);
+    }
     if (s < ce) occ_batch<T, VEC, K, OB, LOSS, true, GC, UNI>(cd, s, ce, rv, G2, cr);
 }
 
@@ -606,9 +614,9 @@ __device__ __forceinline__ void var_gather(int kk, const uint32_t* cd, int cs, i
 #pragma unroll
     for (int h = 0; h < H; ++h) G2[h] = dup2(0.0f);
     switch (kk) {
-        case 1: var_occ_fixed<T, VEC, 1, LOSS, GC, UNI>(cd, cs, ce, rv, G2, cr); break;
-        case 2: var_occ_fixed<T, VEC, 2, LOSS, GC, UNI>(cd, cs, ce, rv, G2, cr); break;
-        case 3: var_occ_fixed<T, VEC, 3, LOSS, GC, UNI>(cd, cs, ce, rv, G2, cr); break;
+        case 1: var_occ_fixed<T, VEC, 1, LOSS, GC, UNI>(cd, cs, ce, cc, rv, G2, cr); break;
+        case 2: var_occ_fixed<T, VEC, 2, LOSS, GC, UNI>(cd, cs, ce, cc, rv, G2, cr); break;
+        case 3: var_occ_fixed<T, VEC, 3, LOSS, GC, UNI>(cd, cs, ce, cc, rv, G2, cr); break;
         default: var_slots<T, VEC, NB, LOSS, GC, UNI>(cd, cs, ce, cc, rv, G2, cr); break;
     }
 #pragma unroll
