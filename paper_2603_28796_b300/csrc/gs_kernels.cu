@@ -868,9 +868,9 @@ __global__ void __launch_bounds__(kThreads) k_check(const CheckParams P) {
     const int total = P.n_items * P.n_wchunks;
     // 32-bit words (B <= 32): each warp takes a fixed contiguous range of tiles instead of
     // pulling from the queue, so a CTA's warps work on neighbouring tiles (with tiles sorted by
-    // median row, the same rows); the kernel runs 2 CTAs per SM and leaves the rest of the
+    // median row, the same rows); the kernel runs 3 CTAs per SM and leaves the rest of the
     // SM's memory to L1, where those rows' compact words stay (community formula: 1.78 ->
-    // 0.84 ms per check)
+    // 0.79 ms per check)
     constexpr bool STATIC = sizeof(W) == 4;
     const int gw = blockIdx.x * kWarps + warp, nw = gridDim.x * kWarps;
     const int per = (total + nw - 1) / nw;
@@ -1224,12 +1224,14 @@ int check_grid_t() {
     static int grid = 0;
     if (!grid) {
         if constexpr (sizeof(W) == 4) {
-            // two CTAs per SM (83 KB of staging buffers) and a 40 % shared-memory carveout: the
-            // rest of the SM's memory is L1 for the gathered words
+            // three CTAs per SM (126 KB of staging buffers) and a 57 % shared-memory carve-out
+            // (the 132 KB configuration): the other 124 KB of the SM's memory is L1 for the
+            // gathered words (community formula: 0.79 ms per check, against 0.84 with two CTAs
+            // and 152 KB of L1, 0.97 with four and 60 KB)
             auto kernel = k_check<LW, W>;
             cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kWarps * kFwdWarpBytes);
-            cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 40);
-            grid = 2 * sm_count();
+            cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 57);
+            grid = 3 * sm_count();
         } else {
             grid = persistent_grid(k_check<LW, W>, kWarps * kFwdWarpBytes);
         }
