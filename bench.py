@@ -387,7 +387,9 @@ def leg_structured(torch, args, peak):
 
 def leg_batching(torch, args, peak):
     """512 uneven instances, B=64 each: one batched problem stepped by one persistent launch
-    per kernel, vs a loop over 512 separately loaded problems stepping the same state rows."""
+    per kernel, vs a loop over 512 separately loaded problems stepping the same state rows; then
+    the same batch with BF16 storage (steps/s against FP32 and the gradient error of BF16
+    storage)."""
     from paper_2603_28796_b300 import _abi
     from paper_2603_28796_b300.engine import Engine
 
@@ -463,6 +465,52 @@ def leg_batching(torch, args, peak):
         p.close()
     del eng
     prob.close()
+    torch.cuda.empty_cache()
+
+    # The same batch with BF16 storage of the relaxed values (FP32 accumulation and Adam state),
+    # its steps/s against the FP32 batch above, and the gradient error of BF16 storage against
+    # FP32 storage at the same logits (seeded normal logits, scale 2).
+    from paper_2603_28796_b300.engine import candidates
+    prob16, tuning16 = load_tuned(batch, B, "bf16", search_tiles=False)
+    eng16 = Engine(prob16, B, "bf16", seed=31)
+    ms16, step16 = _timed_steps(torch, eng16, max(5, args.leg_steps // 5), args.warmup)
+    gm16 = _gather_model_bytes(nnz, n, B, 2)
+    cb16 = _compulsory_bytes(n, B, 2)
+    out["batched_bf16"] = {"ms_per_step": ms16, "steps_per_s": 1000.0 / ms16, "evals_per_s": nnz * B / (ms16 / 1000.0),
+                           "gs_step_ms": step16, "gather_model_frac": gm16 / (step16 / 1000.0) / 1e9 / peak,
+                           "compulsory_frac": cb16 / (step16 / 1000.0) / 1e9 / peak, "tuning": tuning16,
+                           **_row_read_stats(prob16, B, 2, step16)}
+    out["bf16_speedup"] = ms / ms16
+    del eng16
+    torch.cuda.empty_cache()
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(37)
+    delta = candidates(n, B)
+    delta.normal_(0.0, 2.0, generator=gen)
+    x32, x16 = candidates(n, B), candidates(n, B, torch.bfloat16)
+    _abi.gs_relax(prob16, delta, x32)
+    _abi.gs_relax(prob16, delta, x16)
+    del delta
+    g32 = _abi.gs_backward(prob16, x32)
+    del x32
+    g16 = _abi.gs_backward(prob16, x16)
+    del x16
+    sq_d = sq_r = 0.0
+    max_d = 0.0
+    agree = 0
+    for r0 in range(0, n, 1 << 20):
+        a32 = g32[r0:r0 + (1 << 20)].double()
+        d = g16[r0:r0 + (1 << 20)].double() - a32
+        sq_d += float(d.pow(2).sum())
+        sq_r += float(a32.pow(2).sum())
+        max_d = max(max_d, float(d.abs().max()))
+        agree += int(((a32 + d > 0) == (a32 > 0)).sum())
+    rms = (sq_r / (n * B)) ** 0.5
+    out["grad_error_bf16_vs_f32"] = {
+        "rel_l2": (sq_d / sq_r) ** 0.5, "max_abs_over_rms": max_d / rms, "sign_agreement": agree / (n * B),
+        "note": "gradients at the same float32 logits; x stored as BF16 (round to nearest even) vs FP32"}
+    del g32, g16
+    prob16.close()
     torch.cuda.empty_cache()
     return out
 

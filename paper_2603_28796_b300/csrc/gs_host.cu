@@ -726,11 +726,13 @@ gs_status gs_autotune(gs_problem* p, int32_t B, gs_dtype dtype, gs_stream stream
         if (out) gs_get_tuning(p, out);
         return GS_OK;
     }
-    // temporary candidate arrays: delta, m, v, grad (float) and two value buffers (dtype)
+    // temporary candidate arrays: delta, m, v (float), two value buffers (dtype) and the loss
+    // output, one row of B doubles per instance
     const size_t es = (static_cast<int>(dtype) == kF32) ? 4 : 2;
     const size_t fbytes = static_cast<size_t>(n) * ldB * 4, xbytes = static_cast<size_t>(n) * ldB * es;
+    const size_t lbytes = static_cast<size_t>(std::max(p->h.n_inst, 1)) * static_cast<size_t>(B) * sizeof(double);
     void* mem = nullptr;
-    if (cudaMalloc(&mem, 3 * fbytes + 2 * xbytes + static_cast<size_t>(B) * 8 + 256) != cudaSuccess) {
+    if (cudaMalloc(&mem, 3 * fbytes + 2 * xbytes + lbytes + 256) != cudaSuccess) {
         cudaGetLastError();
         return fail(GS_ERR_OOM, "gs_autotune temporaries");
     }

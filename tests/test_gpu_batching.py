@@ -10,6 +10,7 @@ The batch mixes planted 3-SAT (clause/variable ratio uniform in [4.0, 4.26]) and
 - one fused step, per instance, on sampled candidate columns against the FP64 oracle (candidates
   are independent, so a column sample is exact): the per-instance loss within 1e-5, Adam within
   the propagated bound, the rounded bits equal to [delta' > 0], and the unsat counts bit-exact.
+Both run with FP32 and with BF16 storage of the relaxed values.
 """
 import numpy as np
 import pytest
@@ -43,11 +44,12 @@ def batch_prob():
     prob.close()
 
 
+@pytest.mark.parametrize("dtype", ["f32", "bf16"])
 @pytest.mark.parametrize("split", [1, 2])
-def test_uneven_batch_graph_replay_equals_eager(batch_prob, split):
+def test_uneven_batch_graph_replay_equals_eager(batch_prob, split, dtype):
     parts, batch, prob = batch_prob
     _abi.gs_set_tuning(prob, var_split=split, loss_mode=1)
-    e1, e2 = Engine(prob, B, "f32", seed=81), Engine(prob, B, "f32", seed=81)
+    e1, e2 = Engine(prob, B, dtype, seed=81), Engine(prob, B, dtype, seed=81)
     for _ in range(4):
         e1.step()
     g = e2.capture(4)
@@ -61,9 +63,12 @@ def test_uneven_batch_graph_replay_equals_eager(batch_prob, split):
     _abi.gs_set_tuning(prob)
 
 
-def test_uneven_batch_step_matches_oracle_per_instance(batch_prob):
+@pytest.mark.parametrize("dtype", ["f32", "bf16"])
+def test_uneven_batch_step_matches_oracle_per_instance(batch_prob, dtype):
+    """With BF16 storage the oracle runs at the stored (rounded) values, so the bars are the
+    FP32-accumulation ones."""
     parts, batch, prob = batch_prob
-    eng = Engine(prob, B, "f32", seed=82)
+    eng = Engine(prob, B, dtype, seed=82)
     for _ in range(2):
         eng.step()
     torch.cuda.synchronize()

@@ -325,6 +325,38 @@ def test_batch_instances_fused_step(dtype, split):
     prob.close()
 
 
+@pytest.mark.parametrize("dtype", ["f32", "bf16"])
+def test_autotune_on_batch(dtype):
+    """gs_autotune on a batch of many instances: its timed steps write one loss row per instance
+    into its own temporaries. It returns valid settings, the problem stays usable, and a step
+    with the chosen settings matches the oracle per instance."""
+    parts = [synth.planted_ksat(200 + 10 * i, int(4.2 * (200 + 10 * i)), 3 + (i % 2), seed=400 + i)
+             for i in range(40)]
+    batch = synth.concat(parts)
+    prob = _abi.gs_load_batch(batch.n_vars, batch.n_clauses, batch.clause_ptr, batch.lits)
+    B = 64
+    tuned = _abi.gs_autotune(prob, B, dtype)
+    assert tuned["var_lanes"] in (4, 8, 16, 32) and tuned["var_split"] in (1, 2)
+    assert tuned["loss_mode"] in (1, 2) and tuned["var_gather"] in (1, 2)
+    _abi.gs_sync_status(prob)
+    n = int(batch.n_vars.sum())
+    eng = Engine(prob, B, dtype, seed=401)
+    x0 = H.host64(eng.x_cur)
+    eng.step()
+    torch.cuda.synchronize()
+    loss = eng.loss.cpu().numpy()
+    assert loss.shape == (len(parts), B)
+    off = 0
+    for i, p in enumerate(parts):
+        lu, _ = oracle.forward(p.n_vars, p.clause_ptr, p.lits, x0[off:off + p.n_vars])
+        H.assert_loss(loss[i], lu, "instance %d loss after autotune" % i)
+        off += p.n_vars
+    assert off == n
+    _abi.gs_sync_status(prob)
+    del eng
+    prob.close()
+
+
 def test_deterministic_bitwise():
     cnf, prob = get("mixed")
     B = 128
